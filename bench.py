@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Throughput of the fused volumetric-curvilinear stream-and-collide step.
+
+Workload: D3Q19, 256^3 cells, FP32 populations, a channel with tanh wall-normal
+stretching and a sinusoidal bump on the lower wall (amplitude 0.05 h,
+wavelength half the streamwise length), walls with halfway bounce-back,
+periodic streamwise and spanwise axes, constant body force, tau = 0.6, rho = 1
+with seeded 1% velocity noise. A step is one time step over the whole lattice
+(one fused kernel launch). Metric: MLUPS (million cell updates per second) and
+the fraction of the measured HBM copy bandwidth that the algorithmic traffic
+(each population read and written once, 2 * 19 * 4 = 152 bytes per cell
+update) reaches.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas of the workload,
+no collective on the data path (weak scaling); timing is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {("19", "f32"): 2 * 19 * 4, ("19", "f64"): 2 * 19 * 8, ("9", "f32"): 2 * 9 * 4,
+                  ("9", "f64"): 2 * 9 * 8}
+STEP_SOURCES = ["vlb_step.cu", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_internal.cuh"]
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per axis")
+    ap.add_argument("--stretch", type=float, default=0.7)
+    ap.add_argument("--coef-mode", default="auto", choices=["auto", "full", "plane"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2401_17183_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(ncell):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current step-kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "step_d3q19_f32_channel_ncu.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_cell_update:\s*([0-9.]+)", txt)
+    if not m_sha or not m_b or m_sha.group(1) != source_sha():
+        return None
+    return float(m_b.group(1)) * ncell
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.path = os.path.join("/tmp", "vlb_clocks_%d_%d.csv" % (os.getpid(), int(time.time())))
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_id)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+def reference_sample_run(steps, warmup, budget_s=120.0):
+    """The FP64 oracle on the host cores, on a bounded sample of the channel family."""
+    from oracle import OracleSim
+    from paper_2401_17183_gb300 import workloads as W
+    prm = W.params(0.6, body_force=(1e-6, 0.0, 0.0))
+
+    def run(s, k):
+        mesh = W.channel_mesh(s, s, s, stretch=0.7, bump=0.05)
+        rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+        o = OracleSim(mesh, prm)
+        o.init(rho, u)
+        t = time.perf_counter()
+        o.step(k)
+        return time.perf_counter() - t, s ** 3
+
+    dt, nc = run(6, 1)
+    per_cell = dt / nc
+    per_step_budget = budget_s / max(1, steps + warmup)
+    s = 4
+    while (s + 2) ** 3 * per_cell <= per_step_budget and s < 32:
+        s += 2
+    mesh = W.channel_mesh(s, s, s, stretch=0.7, bump=0.05)
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+    o = OracleSim(mesh, prm)
+    o.init(rho, u)
+    o.step(warmup)
+    t = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t
+    return {"value": s ** 3 * steps / el / 1e6, "cells": s ** 3, "steps": steps, "seconds": el,
+            "sample": "%d^3 cells of the same channel family (stretch 0.7, bump 0.05 h, walls, "
+                      "body force, tau 0.6), %d timed steps" % (s, steps)}
+
+
+def cpu_baseline_leg():
+    """Oracle MLUPS on a bounded sample (about 10-20 s of CPU work), 1 thread."""
+    from oracle import OracleSim
+    from paper_2401_17183_gb300 import workloads as W
+    prm = W.params(0.6, body_force=(1e-6, 0.0, 0.0))
+    mesh = W.channel_mesh(32, 32, 16, stretch=0.7, bump=0.05)
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+    o = OracleSim(mesh, prm)
+    o.init(rho, u)
+    o.step(1)
+    t = time.perf_counter()
+    k = 0
+    while k < 3 or (time.perf_counter() - t < 12.0 and k < 200):
+        o.step(1)
+        k += 1
+    el = time.perf_counter() - t
+    nc = 32 * 32 * 16
+    return {"value": nc * k / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": "32x32x16 cells of the same channel family (D3Q19, FP64, stretch 0.7, "
+                      "bump 0.05 h), %d steps, %.1f s, single thread" % (k, el)}
+
+
+def main():
+    a = args_parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    metric = "MLUPS & % HBM roofline (fused D3Q19 stream-and-collide step)"
+    cfg = {"workload": "channel_d3q19_%d^3_fp32" % a.n, "cells": a.n ** 3, "lattice": "D3Q19",
+           "stretch": a.stretch, "bump": 0.05, "tau": 0.6, "walls": "eta (halfway bounce-back)",
+           "periodic": "xi, zeta", "body_force": 1e-6,
+           "l2": "no flush: populations %.2f GB > 129 MB L2" % (a.n ** 3 * 152 / 2 / 1e9)}
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        r = reference_sample_run(a.steps, a.warmup)
+        line = {"impl": "reference", "metric": metric, "value": r["value"], "unit": "MLUPS",
+                "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": 1e3 * r["seconds"] / r["steps"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": cfg,
+                "cpu_baseline": {"value": r["value"], "unit": "MLUPS", "cores": 1,
+                                 "kind": "oracle", "sample": r["sample"], "cpu": cpu_model()},
+                "e2e": {"value": r["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2401_17183_gb300 import build as B
+    B.build()
+    from paper_2401_17183_gb300 import vlb
+    from paper_2401_17183_gb300 import workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    mesh = W.channel_mesh(a.n, a.n, a.n, stretch=a.stretch, bump=0.05)
+    prm = W.params(0.6, body_force=(1e-6, 0.0, 0.0))
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+    ncell = W.ncell(mesh)
+    gmesh = vlb.Mesh(mesh)
+    info = gmesh.info()
+    mode = {"auto": vlb.VLB_COEF_AUTO, "full": vlb.VLB_COEF_FULL, "plane": vlb.VLB_COEF_PLANE}[a.coef_mode]
+    sim = vlb.Sim(gmesh, prm, rho, u, precision=vlb.VLB_F32, coef_mode=mode,
+                  stream=stream.cuda_stream)
+    lay = sim.layout()
+    cfg["coef_mode"] = "plane" if lay["plane"] else "full"
+    cfg["feq_rest_min"] = info["feq_rest_min"]
+
+    # ---- device-resident timing
+    sim.step(a.warmup)
+    sim.sync()
+    gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(a.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    sim.sync()     # raises on a kernel-reported error (e.g. a non-converged solve)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncell * a.steps / (ms / 1e3) / 1e6
+    per_launch_s = ms / 1e3 / a.steps
+    bpc = BYTES_PER_CELL[("19", "f32")]
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bpc * ncell / per_launch_s / 1e9
+    traffic = ncu_traffic(ncell)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        pin_rho = torch.from_numpy(rho).pin_memory()
+        pin_u = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+        out_rho = torch.empty(ncell, dtype=torch.float64).pin_memory()
+        out_u = torch.empty(ncell * 3, dtype=torch.float64).pin_memory()
+        out_ut = torch.empty(ncell * 3, dtype=torch.float64).pin_memory()
+        out_t = torch.empty(7, dtype=torch.float64).pin_memory()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sim.reset_ptr(pin_rho.data_ptr(), pin_u.data_ptr())
+        sim.step(a.steps)
+        sim.moments_ptr(out_rho.data_ptr(), out_u.data_ptr(), out_ut.data_ptr(), out_t.data_ptr())
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = 8 * ncell * 4
+        d2h = 8 * ncell * 7 + 56
+        e2e = {"value": world * ncell * a.steps / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
+               "api": "vlb_reset(host rho,u) + vlb_step(K) + vlb_moments(host rho,u,u~,totals)"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline_leg()
+    line = {
+        "metric": metric, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded mesh and 1% velocity noise)", "config": cfg,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes_per_cell_update": bpc, "kernel": "k_step<19,float,float>",
+                     "source_sha": source_sha()},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": a.steps, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * vlb.h -- C-ABI of the GB300 (sm_103a) volumetric lattice Boltzmann library
+ * for general curvilinear meshes (H. Chen, "Volumetric Lattice Boltzmann
+ * Models in General Curvilinear Coordinates: Theoretical Formulation").
+ *
+ * The paper's problem statement (section 2): given the node positions x(q)
+ * of a structured mesh, indexed by the unit-spaced integer lattice q (section
+ * 2.1), advance the cell-volume-weighted populations N_a = J f_a (Eq. 14) by
+ *     N_a(q + c_a, t + 1) = N_a(q, t) + Omega_a(q, t) + deltaN_a(q, t)   (Eq. 12)
+ * with BGK collision (Eq. 20), the curvilinear equilibrium (Eq. 33), the
+ * discrete inertial force (Eqs. 27, 30, 31) and exact one-to-one advection
+ * (Eq. 22), and map the result back to Euclidean fields (Eq. 34).
+ *
+ * Conventions shared by every entry point:
+ *   - Status: every function returns VLB_OK (0) or a VLB_E* code; no C++
+ *     exception crosses this boundary. vlb_last_error() returns a
+ *     thread-local message describing the most recent failure.
+ *   - Memory: all pointer arguments are HOST pointers owned by the caller
+ *     and are only read or written during the call (inputs are copied).
+ *     The library owns all device memory and frees it in the matching
+ *     destroy call.
+ *   - Layout: cell arrays are C-ordered [n0][n1][n2] (axis 2 fastest; n2 = 1
+ *     in 2D); vector fields append a trailing [dim] axis. Population arrays
+ *     are [q][n0][n1][n2] in the library's velocity order, which
+ *     vlb_lattice() reports.
+ *   - Streams: work is issued on params.stream (a cudaStream_t; NULL means
+ *     the legacy default stream). vlb_step is asynchronous; calls that
+ *     return host data synchronise the stream first.
+ *   - Errors raised inside kernels (a fixed-point solve that hit its
+ *     iteration cap) are sticky: they are reported by the next call that
+ *     synchronises (vlb_sync, vlb_moments, vlb_get_state).
+ */
+#ifndef VLB_H
+#define VLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum vlb_status {
+  VLB_OK = 0,
+  VLB_EINVAL = 1,      /* bad argument, shape or unsupported combination */
+  VLB_EGEOM = 2,       /* degenerate mesh: J <= 0 or |D_i - D_-i| = 0 (Eqs. 3, 5) */
+  VLB_ENOCONV = 3,     /* the local implicit solve for F hit its iteration cap */
+  VLB_ENOMEM = 4,      /* device or host allocation failed */
+  VLB_ECUDA = 5,       /* a CUDA runtime call failed */
+  VLB_ENONFINITE = 6   /* non-finite population or moment detected */
+};
+
+enum vlb_lattice_kind { VLB_D2Q9 = 9, VLB_D3Q19 = 19 };
+enum vlb_bc { VLB_PERIODIC = 0, VLB_WALL = 1 };
+enum vlb_precision { VLB_F64 = 0, VLB_F32 = 1 };
+enum vlb_coef_mode { VLB_COEF_AUTO = 0, VLB_COEF_FULL = 1, VLB_COEF_PLANE = 2 };
+enum vlb_wall_links { VLB_WALL_LINKS_ZERO = 0, VLB_WALL_LINKS_GHOST = 1 };
+
+typedef struct vlb_mesh vlb_mesh; /* opaque, library-owned */
+typedef struct vlb_sim vlb_sim;   /* opaque, library-owned */
+
+/* Mesh description (section 2.1).
+ *   x            host [n0][n1][n2][dim] node positions, copied by vlb_mesh_create
+ *   bc[a]        VLB_PERIODIC or VLB_WALL for index axis a (axes >= dim ignored)
+ *   period_shift periodic image across the +end of axis a:
+ *   period_rot     x(q + n_a e_a) = R_a x(q) + shift_a, R_a row-major 3x3
+ *                  (an all-zero matrix means identity; 2D uses its 2x2 block)
+ *   dx           the representative spacing Delta x of Eq. 3; <= 0 means 1
+ *   wall_links   Theta (Eq. 11) on links that cross a wall: VLB_WALL_LINKS_ZERO
+ *                (the reflected particle never travels the link, Theta = 0) or
+ *                VLB_WALL_LINKS_GHOST (Theta from the ghost nodes)
+ * Behind a wall the ghost nodes needed by Eq. 1 are linear extrapolations of
+ * the two nearest interior nodes along that axis. */
+typedef struct {
+  int32_t dim;      /* 2 or 3 */
+  int32_t lattice;  /* VLB_D2Q9 with dim 2, VLB_D3Q19 with dim 3 */
+  int64_t n[3];     /* nodes per index axis, each >= 1 (>= 2 on a wall axis); n[2] = 1 in 2D */
+  const double *x;
+  int32_t bc[3];
+  double period_shift[3][3];
+  double period_rot[3][9];
+  double dx;
+  int32_t wall_links;
+} vlb_mesh_desc;
+
+/* Run parameters.
+ *   tau          BGK relaxation time (Eq. 20), > 1/2
+ *   precision    VLB_F64: FP64 populations and arithmetic;
+ *                VLB_F32: FP32 populations, FP32 arithmetic, FP32 coefficients
+ *                rounded from the FP64 precompute
+ *   coef_mode    VLB_COEF_FULL streams one coefficient record per cell;
+ *                VLB_COEF_PLANE stores one record per column of the fastest
+ *                axis and is only accepted when the mesh geometry does not
+ *                vary along that axis (checked to 1e-12 relative);
+ *                VLB_COEF_AUTO picks PLANE when allowed, else FULL
+ *   body_force   Euclidean acceleration G; adds rho G.g^i to F^i
+ *   wall_u, wall_omega
+ *                rigid motion of the wall on axis a, side s (0: index 0,
+ *                1: index n-1): u_wall = wall_u + wall_omega x x_wall, with
+ *                x_wall halfway between the boundary node and its ghost
+ *   max_iter     iteration cap of the local fixed-point solve for F (0: 100)
+ *   tol          its tolerance, max|dF| <= tol * max(rho, |F|)
+ *                (0: 1e-14 in FP64, 1e-6 in FP32; never below 64 ulp of |F|)
+ *   stream       cudaStream_t for all work of the simulation (NULL: default) */
+typedef struct {
+  double tau;
+  int32_t precision;
+  int32_t coef_mode;
+  double body_force[3];
+  double wall_u[3][2][3];
+  double wall_omega[3][2][3];
+  int32_t max_iter;
+  double tol;
+  void *stream;
+} vlb_params;
+
+/* Per-mesh diagnostics filled by vlb_mesh_info. */
+typedef struct {
+  double J_min, J_max;          /* cell volume range (Eq. 5) */
+  double feq_rest_min;          /* min over cells and directions of f^eq_a(rho = 1, U = 0) / w_a;
+                                   negative means the mesh is outside the range where the
+                                   rest state of Eq. 33 is a positive distribution */
+  double ginv_diag_min, ginv_diag_max;
+  int32_t invariant_fast_axis;  /* 1 when the geometry does not vary along the fastest axis */
+  int64_t ncell;
+} vlb_mesh_stats;
+
+/* Velocity set used by the library: c[q][3] (zero-padded) and w[q] (host
+ * outputs, either may be NULL). Section 2.1 lists D3Q19; D2Q9 is its planar
+ * restriction. Weights are the standard ones with T0 = 1/3 (Eq. 10 to 4th order). */
+int vlb_lattice(int32_t lattice, int32_t *c, double *w);
+
+/* Build the mesh and run the FP64 geometry precompute on the current device:
+ * D_{+-i} (Eq. 1), g_i with beta_i (Eq. 3), J (Eq. 5), g^i (Eq. 7), g^ij
+ * (Eq. 8) and the contracted link coefficients
+ *     K^i_a(q) = sum_j c^j_a Theta^i_j(q + c_a, q)     (Eq. 11)
+ * (zero on links that cross a wall). Errors: VLB_EINVAL (shape, lattice,
+ * bc), VLB_EGEOM (degenerate cell), VLB_ENOMEM, VLB_ECUDA. On failure *out is
+ * NULL. Blocks until the precompute is done. */
+int vlb_mesh_create(const vlb_mesh_desc *desc, vlb_mesh **out);
+int vlb_mesh_info(const vlb_mesh *mesh, vlb_mesh_stats *out);
+/* FP64 geometry read-back (host outputs, each may be NULL):
+ * J [ncell], g_low [ncell][dim][dim] (row i = g_i), ginv [ncell][dim][dim],
+ * K [ncell][q][dim] (row a = K_a). */
+int vlb_mesh_geometry(const vlb_mesh *mesh, double *J, double *g_low, double *ginv, double *K);
+void vlb_mesh_destroy(vlb_mesh *mesh);
+
+/* Create a simulation on a mesh and set N_a = J f^eq_a(rho, U, U~ = U)
+ * (Eqs. 14, 33) with U^i = u . g^i. rho [ncell] and u [ncell][dim] are host
+ * arrays (Euclidean velocity). The mesh must outlive the simulation.
+ * Errors: VLB_EINVAL (tau <= 1/2, bad precision or coef_mode, moving walls
+ * on a cell touching two walls), VLB_ENOMEM, VLB_ECUDA. */
+int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, const double *u,
+             vlb_sim **out);
+/* Re-initialise the populations from host fields as vlb_init does (no allocation). */
+int vlb_reset(vlb_sim *sim, const double *rho, const double *u);
+
+/* Advance nsteps time steps (Eq. 12 with Eq. 22), one fused pull-collide-push
+ * kernel launch per step, alternating the two in-place A-A layouts. Returns
+ * after queueing the launches. */
+int vlb_step(vlb_sim *sim, int64_t nsteps);
+
+/* Synchronise the stream and report any sticky kernel error. */
+int vlb_sync(vlb_sim *sim);
+
+/* Moments at the current time (host outputs, each may be NULL):
+ *   rho [ncell]                 rho = sum_a N_a / J           (Eq. 15)
+ *   u [ncell][dim]              u  = U^i g_i                  (Eq. 34)
+ *   u_tilde [ncell][dim]        u~ = U~^i g_i, U~ = U + F/(2 rho) (text after Eq. 32)
+ *   totals[7]                   mass = sum N, P = sum e_a(q) N_a (dim values),
+ *                               M = sum 1/2 [e_a(q) + e_a(q - c_a)] N_a (dim values),
+ *                               laid out [mass, P0, P1, P2, M0, M1, M2], reduced in FP64
+ * F is the converged solution of the same local fixed point the step solves.
+ * Synchronises; returns VLB_ENONFINITE if a moment is not finite. */
+int vlb_moments(vlb_sim *sim, double *rho, double *u, double *u_tilde, double *totals);
+
+/* Arrived populations N_a(q, t) as FP64 [q][ncell] (host), whatever the
+ * in-place layout of the current step parity; and the inverse. */
+int vlb_get_state(vlb_sim *sim, double *N);
+int vlb_set_state(vlb_sim *sim, const double *N);
+
+/* Steps taken since vlb_init / vlb_reset / vlb_set_state. */
+int64_t vlb_time(const vlb_sim *sim);
+/* Bytes per cell of the coefficient record and whether it is one per column
+ * (plane mode); for reporting. */
+int vlb_sim_layout(const vlb_sim *sim, int32_t *coef_per_cell, int32_t *plane_mode,
+                   int64_t *coef_records);
+
+void vlb_destroy(vlb_sim *sim);
+const char *vlb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

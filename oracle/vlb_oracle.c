@@ -232,7 +232,8 @@ int vlbo_cell_geometry(const vlbo_mesh *m, const vlbo_params *prm, const int64_t
       }
     }
     if (wall_axis >= 0) {
-      /* bounce-back link: no advection along a curved path, Theta = 0 */
+      /* bounce-back link; with wall_links = 0 it carries no curved-path
+       * advection and Theta = 0 */
       out->wall_link[a] = 1;
       if (prm) {
         /* rigid wall motion evaluated at the wall point halfway to the ghost node */
@@ -249,7 +250,8 @@ int vlbo_cell_geometry(const vlbo_mesh *m, const vlbo_params *prm, const int64_t
         for (int d = 0; d < 3; d++) uwv[d] += prm->wall_u[wall_axis][side][d];
         for (int i = 0; i < dim; i++) out->uw[a][i] = dot3(uwv, out->g_up[i]);
       }
-      continue;
+      if (m->wall_links != 1) continue;
+      /* wall_links = 1: Theta from the tangents at the extrapolated ghost node */
     }
     double gp[3][3];
     rc = tangents(m, p, gp);

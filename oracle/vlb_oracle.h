@@ -24,8 +24,10 @@
  *   - the implicit relation between F and N' (text after Eq. 31) is solved
  *     by fixed-point iteration from F = 0 until max|dF| <= tol*max(rho,|F|);
  *     the returned N' is evaluated with the final F;
- *   - walls are index-space halfway bounce-back; Theta is zero on links that
- *     cross a wall; ghost nodes behind a wall are linear extrapolations;
+ *   - walls are index-space halfway bounce-back; ghost nodes behind a wall
+ *     are linear extrapolations; on links that cross a wall Theta is either
+ *     zero (wall_links = 0: the reflected particle never travels the link) or
+ *     taken from the ghost nodes (wall_links = 1);
  *     a moving wall subtracts J rho (f^eq_a - f^eq_abar) evaluated with the
  *     paper's equilibrium at rho = 1, U = U~ = U_wall;
  *   - an external body force G adds rho G.g^i to F^i inside the fixed point;
@@ -70,6 +72,8 @@ typedef struct {
   double shift[3][3];      /* periodic image across the +end of axis a: R_a x + shift[a] */
   double rot[3][9];        /* R_a row-major; an all-zero matrix means identity */
   double dx;               /* representative spacing Delta x of Eq. 3; 0 means 1 */
+  int32_t wall_links;      /* Theta on links that cross a wall: 0 zero (the link reflects
+                              in place), 1 from the linearly extrapolated ghost nodes */
 } vlbo_mesh;
 
 typedef struct {

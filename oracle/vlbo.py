@@ -19,7 +19,7 @@ class _Mesh(C.Structure):
     _fields_ = [("dim", C.c_int32), ("q", C.c_int32), ("n", C.c_int64 * 3),
                 ("x", C.POINTER(C.c_double)), ("bc", C.c_int32 * 3),
                 ("shift", (C.c_double * 3) * 3), ("rot", (C.c_double * 9) * 3),
-                ("dx", C.c_double)]
+                ("dx", C.c_double), ("wall_links", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -98,6 +98,7 @@ def _mesh_struct(mesh):
         for k in range(9):
             m.rot[a][k] = float(mesh["rot"][a][k])
     m.dx = float(mesh.get("dx", 1.0))
+    m.wall_links = int(mesh.get("wall_links", 0))
     m.x = _dp(x)
     return m, x
 

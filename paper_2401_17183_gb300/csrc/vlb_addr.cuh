@@ -1,0 +1,99 @@
+// vlb_addr.cuh -- index arithmetic of the structured lattice: coordinates of
+// a cell, its neighbours q +- c_a with periodic wrap, wall crossings, and the
+// A-A read of the arrived populations N_a(q, t) for either layout parity.
+#pragma once
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+struct Grid {
+  int64_t n[3];
+  int64_t s[3];
+  int32_t wall[3];
+};
+
+template <int Q>
+struct Addr {
+  static constexpr int D = Lat<Q>::D;
+  int64_t cell;
+  int64_t ic[3];
+  int64_t dp[3], dm[3];
+  bool lo[3], hi[3];
+
+  __device__ __forceinline__ Addr(const Grid &g, int64_t c) : cell(c) {
+    int64_t r = c;
+    ic[2] = r % g.n[2];
+    r /= g.n[2];
+    ic[1] = r % g.n[1];
+    ic[0] = r / g.n[1];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      dp[d] = (ic[d] == g.n[d] - 1) ? -(g.n[d] - 1) * g.s[d] : g.s[d];
+      dm[d] = (ic[d] == 0) ? (g.n[d] - 1) * g.s[d] : -g.s[d];
+      lo[d] = g.wall[d] && ic[d] == 0;
+      hi[d] = g.wall[d] && ic[d] == g.n[d] - 1;
+    }
+  }
+  __device__ __forceinline__ bool wall_cell() const {
+    bool w = false;
+#pragma unroll
+    for (int d = 0; d < D; d++) w = w || lo[d] || hi[d];
+    return w;
+  }
+  // does q + sg c_a leave the domain through a wall? (a, sg compile-time
+  // constants after unrolling)
+  __device__ __forceinline__ bool crosses(int a, int sg) const {
+    bool x = false;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      const int cd = sg * Lat<Q>::c(a, d);
+      if (cd > 0) x = x || hi[d];
+      if (cd < 0) x = x || lo[d];
+    }
+    return x;
+  }
+  // linear index of q + sg c_a (periodic wrap on every axis)
+  __device__ __forceinline__ int64_t nb(int a, int sg) const {
+    int64_t r = cell;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      const int cd = sg * Lat<Q>::c(a, d);
+      if (cd > 0) r += dp[d];
+      if (cd < 0) r += dm[d];
+    }
+    return r;
+  }
+};
+
+// Arrived populations N_a(q, t). Even parity: slot a of q. Odd parity (the
+// layout an even step leaves behind): slot abar of q - c_a, or slot a of q
+// when q - c_a lies beyond a wall (halfway bounce-back).
+template <int Q, bool ODD, typename S, typename R>
+__device__ __forceinline__ void pull(const S *f, int64_t ps, const Addr<Q> &ad, R (&N)[Q]) {
+#pragma unroll
+  for (int a = 0; a < Q; a++) {
+    if (!ODD || a == 0) {
+      N[a] = static_cast<R>(f[a * ps + ad.cell]);
+    } else {
+      if (ad.crosses(a, -1))
+        N[a] = static_cast<R>(f[a * ps + ad.cell]);
+      else
+        N[a] = static_cast<R>(f[lat_opp<Q>(a) * ps + ad.nb(a, -1)]);
+    }
+  }
+}
+
+inline Grid make_grid(const vlb_mesh *m) {
+  Grid g;
+  for (int d = 0; d < 3; d++) {
+    g.n[d] = m->md.n[d];
+    g.wall[d] = (d < m->md.dim && m->md.bc[d] == VLB_WALL) ? 1 : 0;
+  }
+  g.s[2] = 1;
+  g.s[1] = g.n[2];
+  g.s[0] = g.n[1] * g.n[2];
+  return g;
+}
+
+}  // namespace vlb

@@ -1,0 +1,558 @@
+// vlb_geometry.cu -- FP64 geometry precompute of section 2.1 (done once per
+// mesh), mesh diagnostics, the coefficient records the step kernel streams,
+// and the equilibrium initialisation of the populations.
+#include "vlb_addr.cuh"
+#include "vlb_collide.cuh"
+
+namespace vlb {
+
+// ------------------------------------------------------------------ positions
+// y <- T_a^k (y), T_a(x) = R_a x + shift_a (inverse for k < 0)
+__device__ __noinline__ void apply_period(const MeshDev &m, int ax, int64_t k, double y[3]) {
+  const int D = m.dim;
+  const double *R = m.rot[ax];
+  const double *sh = m.shift[ax];
+  for (int64_t t = 0; t < (k > 0 ? k : -k); t++) {
+    double z[3] = {y[0], y[1], y[2]};
+    if (k > 0) {
+      if (m.has_rot[ax])
+        for (int i = 0; i < D; i++) {
+          double acc = 0.0;
+          for (int j = 0; j < D; j++) acc += R[3 * i + j] * z[j];
+          y[i] = acc;
+        }
+      for (int i = 0; i < D; i++) y[i] += sh[i];
+    } else {
+      for (int i = 0; i < D; i++) z[i] -= sh[i];
+      if (m.has_rot[ax]) {
+        for (int i = 0; i < D; i++) {
+          double acc = 0.0;
+          for (int j = 0; j < D; j++) acc += R[3 * j + i] * z[j];
+          y[i] = acc;
+        }
+      } else {
+        for (int i = 0; i < D; i++) y[i] = z[i];
+      }
+    }
+  }
+}
+
+// position of p whose wall-axis coordinates are in range: wrap the periodic
+// axes and apply the image transforms, axis 0 outermost
+__device__ __noinline__ void position_periodic(const MeshDev &m, const int64_t p[3], double out[3]) {
+  int64_t w[3], k[3];
+  for (int a = 0; a < 3; a++) {
+    w[a] = p[a];
+    k[a] = 0;
+    if (a < m.dim && m.bc[a] == VLB_PERIODIC) {
+      int64_t q = p[a] / m.n[a];
+      if (p[a] < 0 && q * m.n[a] != p[a]) q -= 1;  // floor division
+      k[a] = q;
+      w[a] = p[a] - q * m.n[a];
+    }
+  }
+  const int64_t idx = (w[0] * m.n[1] + w[1]) * m.n[2] + w[2];
+  for (int d = 0; d < 3; d++) out[d] = d < m.dim ? m.x[idx * m.dim + d] : 0.0;
+  for (int a = m.dim - 1; a >= 0; a--)
+    if (k[a] != 0) apply_period(m, a, k[a], out);
+}
+
+// position of any index p: behind a wall, linear extrapolation along that axis
+// from the two nearest interior nodes, x(-k) = (1 + k) x(0) - k x(1)
+__device__ __noinline__ void position(const MeshDev &m, const int64_t p[3], double out[3]) {
+  int wa[3], nw = 0;
+  int64_t b0[3], b1[3];
+  double c0[3], c1[3];
+  for (int a = 0; a < m.dim; a++) {
+    if (m.bc[a] != VLB_WALL || (p[a] >= 0 && p[a] < m.n[a])) continue;
+    const int64_t k = p[a] < 0 ? -p[a] : p[a] - (m.n[a] - 1);
+    wa[nw] = a;
+    b0[nw] = p[a] < 0 ? 0 : m.n[a] - 1;
+    b1[nw] = p[a] < 0 ? 1 : m.n[a] - 2;
+    c0[nw] = 1.0 + (double)k;
+    c1[nw] = -(double)k;
+    nw++;
+  }
+  out[0] = out[1] = out[2] = 0.0;
+  for (int combo = 0; combo < (1 << nw); combo++) {
+    int64_t pp[3] = {p[0], p[1], p[2]};
+    double wgt = 1.0;
+    for (int t = 0; t < nw; t++) {
+      const bool second = (combo >> t) & 1;
+      pp[wa[t]] = second ? b1[t] : b0[t];
+      wgt *= second ? c1[t] : c0[t];
+    }
+    double y[3];
+    position_periodic(m, pp, y);
+    for (int d = 0; d < 3; d++) out[d] += wgt * y[d];
+  }
+}
+
+__device__ __forceinline__ double nrm(const double v[3]) {
+  return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+// tangent basis g_i(p) (Eqs. 1, 3); false on a folded arm (D_i = D_-i)
+__device__ __noinline__ bool tangents(const MeshDev &m, const int64_t p[3], double gl[3][3]) {
+  const double dx = m.dx > 0.0 ? m.dx : 1.0;
+  double x0[3];
+  position(m, p, x0);
+  bool ok = true;
+  for (int i = 0; i < 3; i++)
+    for (int d = 0; d < 3; d++) gl[i][d] = 0.0;
+  for (int i = 0; i < m.dim; i++) {
+    int64_t pp[3] = {p[0], p[1], p[2]}, pm[3] = {p[0], p[1], p[2]};
+    pp[i] += 1;
+    pm[i] -= 1;
+    double xp[3], xm[3], Dp[3], Dm[3], df[3];
+    position(m, pp, xp);
+    position(m, pm, xm);
+    for (int d = 0; d < 3; d++) {
+      Dp[d] = xp[d] - x0[d];
+      Dm[d] = xm[d] - x0[d];
+      df[d] = Dp[d] - Dm[d];
+    }
+    const double nd = nrm(df);
+    if (!(nd > 0.0)) {
+      ok = false;
+      continue;
+    }
+    const double beta = (nrm(Dp) + nrm(Dm)) / nd;
+    for (int d = 0; d < 3; d++) gl[i][d] = beta * df[d] / (2.0 * dx);
+  }
+  return ok;
+}
+
+// J (Eq. 5) and co-tangents g^i (Eq. 7); in 2D the third tangent is z
+__device__ __noinline__ bool dual(int dim, const double gl[3][3], double &J, double gu[3][3]) {
+  for (int i = 0; i < 3; i++)
+    for (int d = 0; d < 3; d++) gu[i][d] = 0.0;
+  if (dim == 2) {
+    J = gl[0][0] * gl[1][1] - gl[0][1] * gl[1][0];
+    if (!(J > 0.0)) return false;
+    gu[0][0] = gl[1][1] / J;
+    gu[0][1] = -gl[1][0] / J;
+    gu[1][0] = -gl[0][1] / J;
+    gu[1][1] = gl[0][0] / J;
+    return true;
+  }
+  double c12[3], c23[3], c31[3];
+  auto cross = [](const double *a, const double *b, double *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+  };
+  cross(gl[0], gl[1], c12);
+  cross(gl[1], gl[2], c23);
+  cross(gl[2], gl[0], c31);
+  J = c12[0] * gl[2][0] + c12[1] * gl[2][1] + c12[2] * gl[2][2];
+  if (!(J > 0.0)) return false;
+  for (int d = 0; d < 3; d++) {
+    gu[0][d] = c23[d] / J;
+    gu[1][d] = c31[d] / J;
+    gu[2][d] = c12[d] / J;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ precompute
+template <int Q>
+__global__ void k_geometry(const MeshDev m, Grid g, int64_t ncell, double *J_out, double *gl_out,
+                           double *gu_out, double *ginv_out, double *K_out, int *err) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= ncell) return;
+  const Addr<Q> ad(g, cell);
+  const int64_t q[3] = {ad.ic[0], ad.ic[1], ad.ic[2]};
+  double gl[3][3], gu[3][3], J = 0.0;
+  bool ok = tangents(m, q, gl);
+  ok = ok && dual(D, gl, J, gu);
+  if (!ok) {
+    atomicOr(err, ERR_GEOM);
+    J = nan("");
+  }
+  J_out[cell] = J;
+  for (int i = 0; i < D; i++)
+    for (int d = 0; d < D; d++) {
+      gl_out[(cell * D + i) * D + d] = gl[i][d];
+      gu_out[(cell * D + i) * D + d] = gu[i][d];
+    }
+  for (int i = 0; i < D; i++)
+    for (int j = i; j < D; j++) {
+      double s = 0.0;
+      for (int d = 0; d < 3; d++) s += gu[i][d] * gu[j][d];  // g^ij = g^i . g^j (Eq. 8)
+      ginv_out[cell * NS + sym<D>(i, j)] = s;
+    }
+  for (int i = 0; i < D; i++) K_out[(cell * Q + 0) * D + i] = 0.0;
+  // K^i_a = sum_j c^j_a [g_j(q + c_a) - g_j(q)] . g^i(q) = sum_j c^j_a Theta^i_j(q + c_a, q) (Eq. 11)
+#pragma unroll 1
+  for (int a = 1; a < Q; a++) {
+    double Kv[3] = {0.0, 0.0, 0.0};
+    // links that cross a wall: zero, or from the ghost-node tangents
+    if (!ad.crosses(a, 1) || m.wall_links == VLB_WALL_LINKS_GHOST) {
+      int64_t p[3] = {q[0], q[1], q[2]};
+      for (int d = 0; d < D; d++) p[d] += Lat<Q>::c(a, d);
+      double gp[3][3];
+      if (!tangents(m, p, gp)) atomicOr(err, ERR_GEOM);
+      double de[3] = {0.0, 0.0, 0.0};
+      for (int j = 0; j < D; j++) {
+        const int cj = Lat<Q>::c(a, j);
+        if (cj == 0) continue;
+        for (int d = 0; d < 3; d++) de[d] += cj * (gp[j][d] - gl[j][d]);
+      }
+      for (int i = 0; i < D; i++) Kv[i] = de[0] * gu[i][0] + de[1] * gu[i][1] + de[2] * gu[i][2];
+    }
+    for (int i = 0; i < D; i++) K_out[(cell * Q + a) * D + i] = Kv[i];
+  }
+}
+
+cudaError_t launch_geometry(const vlb_mesh *m, int *d_err, cudaStream_t s) {
+  const int threads = 128;
+  const int64_t blocks = (m->ncell + threads - 1) / threads;
+  const Grid g = make_grid(m);
+  if (m->md.q == 9)
+    k_geometry<9><<<(unsigned)blocks, threads, 0, s>>>(m->md, g, m->ncell, m->d_J, m->d_gl,
+                                                       m->d_gu, m->d_ginv, m->d_K, d_err);
+  else
+    k_geometry<19><<<(unsigned)blocks, threads, 0, s>>>(m->md, g, m->ncell, m->d_J, m->d_gl,
+                                                        m->d_gu, m->d_ginv, m->d_K, d_err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ diagnostics
+// per block: [min J, -max J, min f^eq_rest/w, min g^ii, -max g^ii], reduced on the host
+template <int Q>
+__global__ void k_mesh_stats(const double *J, const double *ginv, int64_t ncell,
+                             double *partial) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
+  __shared__ double sh[5][kStatThreads];
+  double v[5] = {1e300, 1e300, 1e300, 1e300, 1e300};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    v[0] = fmin(v[0], J[c]);
+    v[1] = fmin(v[1], -J[c]);
+    double gi[NS], U[D], Ut[D];
+    for (int i = 0; i < NS; i++) gi[i] = ginv[c * NS + i];
+    for (int i = 0; i < D; i++) U[i] = Ut[i] = 0.0;
+    EqParts<Q, double> e;
+    eq_parts<Q, double>(gi, U, Ut, e);
+    double m = eq_even<Q, double>(e, 0);
+#pragma unroll
+    for (int p = 1; p <= H; p++) m = fmin(m, eq_even<Q, double>(e, p));
+    v[2] = fmin(v[2], m);
+    for (int i = 0; i < D; i++) {
+      v[3] = fmin(v[3], gi[sym<D>(i, i)]);
+      v[4] = fmin(v[4], -gi[sym<D>(i, i)]);
+    }
+  }
+  for (int k = 0; k < 5; k++) sh[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < 5; k++) sh[k][threadIdx.x] = fmin(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; k++) partial[blockIdx.x * 5 + k] = sh[k][0];
+}
+
+cudaError_t launch_mesh_stats(const vlb_mesh *m, double *d_partial, int64_t nblk, cudaStream_t s) {
+  if (m->md.q == 9)
+    k_mesh_stats<9><<<(unsigned)nblk, kStatThreads, 0, s>>>(m->d_J, m->d_ginv, m->ncell, d_partial);
+  else
+    k_mesh_stats<19><<<(unsigned)nblk, kStatThreads, 0, s>>>(m->d_J, m->d_ginv, m->ncell, d_partial);
+  return cudaGetLastError();
+}
+
+// plane check: does every cell's geometry equal that of the first cell of its
+// column along the fastest axis (to 1e-12 relative)?
+__device__ __forceinline__ bool close12(double a, double b) {
+  return fabs(a - b) <= 1e-12 * (1.0 + fabs(b));
+}
+
+template <int Q>
+__global__ void k_plane_check(const double *J, const double *ginv, const double *gu,
+                              const double *K, int64_t ncell, int64_t nfast, int *flag) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int64_t c0 = (c / nfast) * nfast;
+  if (c0 == c) return;
+  bool same = close12(J[c], J[c0]);
+  for (int i = 0; i < NS; i++) same = same && close12(ginv[c * NS + i], ginv[c0 * NS + i]);
+  for (int i = 0; i < D * D; i++) same = same && close12(gu[c * D * D + i], gu[c0 * D * D + i]);
+  for (int i = 0; i < Q * D; i++) same = same && close12(K[c * Q * D + i], K[c0 * Q * D + i]);
+  if (!same) atomicOr(flag, 1);
+}
+
+cudaError_t launch_plane_check(const vlb_mesh *m, int *d_flag, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t blocks = (m->ncell + threads - 1) / threads;
+  const int64_t nfast = m->md.n[m->md.dim - 1];
+  if (m->md.q == 9)
+    k_plane_check<9><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_ginv, m->d_gu, m->d_K,
+                                                          m->ncell, nfast, d_flag);
+  else
+    k_plane_check<19><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_ginv, m->d_gu, m->d_K,
+                                                           m->ncell, nfast, d_flag);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ coefficient records
+struct PackArgs {
+  MeshDev md;
+  Grid g;
+  const double *J, *gu, *ginv, *K;
+  int64_t nrec, stride, nfast;
+  int32_t plane;
+  double tau;
+  double body[3];
+  double wall_u[3][2][3];
+  double wall_omega[3][2][3];
+};
+
+// Geometric part L of the Jacobian dG/dF of the fixed-point map of Eq. 27
+// (the terms that do not vanish with U): with
+//   h^l_a = 9/4 [(c.g.c) c^l - T0 (2 (g c)^l + tr(g) c^l)]      (d x_a / dF^l = h^l_a / rho)
+//   P^{ijl} = 2 cpi sum_p w_p c^i_p (K^j_p + K^j_pbar) h^l_p  (d deltaPi^ij / dF^l)
+//   L^{il} = -1/2 sum_a w_a K^i_a [h^l_a / tau + 3 c^l_a + 3 (3 c_a.P^l.c_a - tr P^l)]
+// returns H = (I - L)^-1.
+template <int Q>
+__device__ void chord_matrix(const CellCoef<Q, double> &k, double tau, double (&Hm)[Lat<Q>::D][Lat<Q>::D]) {
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  const double T0 = kT0, itau = 1.0 / tau, cpi = -0.5 * (1.0 - 0.5 * itau);
+  double g[D][D], trg = 0.0;
+  for (int i = 0; i < D; i++)
+    for (int j = 0; j < D; j++) g[i][j] = k.gi[sym<D>(i, j)];
+  for (int i = 0; i < D; i++) trg += g[i][i];
+  double h[Q][D];
+  for (int a = 0; a < Q; a++) {
+    double c[D], gc[D], cgc = 0.0;
+    for (int i = 0; i < D; i++) c[i] = Lat<Q>::c(a, i);
+    for (int i = 0; i < D; i++) {
+      gc[i] = 0.0;
+      for (int j = 0; j < D; j++) gc[i] += g[i][j] * c[j];
+      cgc += c[i] * gc[i];
+    }
+    for (int l = 0; l < D; l++) h[a][l] = 2.25 * (cgc * c[l] - T0 * (2.0 * gc[l] + trg * c[l]));
+  }
+  double L[D][D];
+  for (int l = 0; l < D; l++) {
+    double P[D][D];
+    for (int i = 0; i < D; i++)
+      for (int j = 0; j < D; j++) {
+        double s = 0.0;
+        for (int p = 1; p <= H; p++)
+          s += lat_w<Q, double>(p) * Lat<Q>::c(p, i) * (k.K[p][j] + k.K[p + H][j]) * h[p][l];
+        P[i][j] = 2.0 * cpi * s;
+      }
+    double trP = 0.0;
+    for (int i = 0; i < D; i++) trP += P[i][i];
+    for (int i = 0; i < D; i++) {
+      double s = 0.0;
+      for (int a = 1; a < Q; a++) {
+        double cPc = 0.0;
+        for (int x = 0; x < D; x++)
+          for (int y = 0; y < D; y++) cPc += Lat<Q>::c(a, x) * Lat<Q>::c(a, y) * P[x][y];
+        s += lat_w<Q, double>(a) * k.K[a][i] *
+             (h[a][l] * itau + 3.0 * Lat<Q>::c(a, l) + 3.0 * (3.0 * cPc - trP));
+      }
+      L[i][l] = -0.5 * s;
+    }
+  }
+  double A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int i = 0; i < D; i++)
+    for (int j = 0; j < D; j++) A[i][j] = (i == j ? 1.0 : 0.0) - L[i][j];
+  if (D == 2) {
+    const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    Hm[0][0] = A[1][1] / det;
+    Hm[0][1] = -A[0][1] / det;
+    Hm[1][0] = -A[1][0] / det;
+    Hm[1][1] = A[0][0] / det;
+  } else {
+    double C[3][3];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        C[j][i] = A[i1][j1] * A[i2][j2] - A[i1][j2] * A[i2][j1];  // adjugate (transposed cofactors)
+      }
+    const double det = A[0][0] * C[0][0] + A[0][1] * C[1][0] + A[0][2] * C[2][0];
+    for (int i = 0; i < D; i++)
+      for (int j = 0; j < D; j++) Hm[i][j] = C[i][j] / det;
+  }
+}
+
+template <int Q, typename R>
+__global__ void k_pack_coef(const PackArgs a, R *coef) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2;
+  using L = CoefLayout<Q>;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.nrec) return;
+  const int64_t c = a.plane ? r * a.nfast : r;
+  const int64_t st = a.stride;
+  coef[L::J * st + r] = static_cast<R>(a.J[c]);
+  for (int i = 0; i < NS; i++) coef[(L::GINV + i) * st + r] = static_cast<R>(a.ginv[c * NS + i]);
+  for (int i = 0; i < D; i++) {
+    double s = 0.0;
+    for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];  // G^i = G . g^i
+    coef[(L::BODY + i) * st + r] = static_cast<R>(s);
+  }
+  for (int av = 1; av < Q; av++)
+    for (int i = 0; i < D; i++)
+      coef[(L::K + (av - 1) * D + i) * st + r] = static_cast<R>(a.K[(c * Q + av) * D + i]);
+  // reference-state part of J F: sum_a w_a K^i_a
+  for (int i = 0; i < D; i++) {
+    double s = 0.0;
+    for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * a.K[(c * Q + av) * D + i];
+    coef[(L::KW + i) * st + r] = static_cast<R>(s);
+  }
+  // chord matrix and rest-state force
+  {
+    CellCoef<Q, double> k;
+    k.J = a.J[c];
+    for (int i = 0; i < NS; i++) k.gi[i] = a.ginv[c * NS + i];
+    for (int i = 0; i < D; i++) {
+      double s = 0.0;
+      for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
+      k.G[i] = s;
+      k.Kw[i] = 0.0;
+      k.Fr[i] = 0.0;
+      for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
+    }
+    for (int av = 0; av < Q; av++)
+      for (int i = 0; i < D; i++) k.K[av][i] = a.K[(c * Q + av) * D + i];
+    double Hm[D][D];
+    chord_matrix<Q>(k, a.tau, Hm);
+    for (int i = 0; i < D; i++)
+      for (int j = 0; j < D; j++) coef[(L::HM + i * D + j) * st + r] = static_cast<R>(Hm[i][j]);
+    // F at rest (rho = 1, U = 0), the start value of the chord iteration
+    double N[Q], U0[D], gi[NS];
+    for (int i = 0; i < D; i++) U0[i] = 0.0;
+    for (int i = 0; i < NS; i++) gi[i] = k.gi[i];
+    EqParts<Q, double> e;
+    eq_parts<Q, double>(gi, U0, U0, e);
+    for (int av = 0; av < Q; av++) {
+      const int p = av <= Lat<Q>::H ? av : av - Lat<Q>::H;
+      N[av] = k.J * lat_w<Q, double>(av) * eq_even<Q, double>(e, p);
+    }
+    double Np[Q];
+    CollideState<Q, double> cs;
+    collide_cell<Q, double, false, false>(N, k, 0.0, a.tau, 1e-15, 400, Np, cs);
+    for (int i = 0; i < D; i++) coef[(L::FR + i) * st + r] = static_cast<R>(cs.conv ? cs.F[i] : 0.0);
+  }
+  // wall velocity: rigid motion of the adjacent wall, at the point halfway to the ghost node
+  const Addr<Q> ad(a.g, c);
+  double uw[3] = {0.0, 0.0, 0.0};
+  for (int ax = 0; ax < D; ax++) {
+    if (!(ad.lo[ax] || ad.hi[ax])) continue;
+    const int side = ad.lo[ax] ? 0 : 1;
+    int64_t q[3] = {ad.ic[0], ad.ic[1], ad.ic[2]}, gq[3] = {ad.ic[0], ad.ic[1], ad.ic[2]};
+    gq[ax] += side ? 1 : -1;
+    double x0[3], xg[3], xw[3], u[3];
+    position(a.md, q, x0);
+    position(a.md, gq, xg);
+    for (int d = 0; d < 3; d++) xw[d] = 0.5 * (x0[d] + xg[d]);
+    const double *om = a.wall_omega[ax][side];
+    u[0] = om[1] * xw[2] - om[2] * xw[1];
+    u[1] = om[2] * xw[0] - om[0] * xw[2];
+    u[2] = om[0] * xw[1] - om[1] * xw[0];
+    for (int d = 0; d < 3; d++) u[d] += a.wall_u[ax][side][d];
+    for (int i = 0; i < D; i++) {
+      double s = 0.0;
+      for (int d = 0; d < D; d++) s += u[d] * a.gu[(c * D + i) * D + d];
+      uw[i] = s;
+    }
+    break;
+  }
+  for (int i = 0; i < D; i++) coef[(L::UW + i) * st + r] = static_cast<R>(uw[i]);
+}
+
+template <int Q>
+static cudaError_t pack_q(const vlb_sim *sim, cudaStream_t s) {
+  const vlb_mesh *m = sim->mesh;
+  PackArgs a;
+  a.md = m->md;
+  a.g = make_grid(m);
+  a.J = m->d_J;
+  a.gu = m->d_gu;
+  a.ginv = m->d_ginv;
+  a.K = m->d_K;
+  a.nrec = sim->ncoef;
+  a.stride = sim->ncoef;
+  a.nfast = m->md.n[m->md.dim - 1];
+  a.plane = sim->plane;
+  a.tau = sim->p.tau;
+  for (int d = 0; d < 3; d++) a.body[d] = sim->p.body_force[d];
+  for (int ax = 0; ax < 3; ax++)
+    for (int sd = 0; sd < 2; sd++)
+      for (int d = 0; d < 3; d++) {
+        a.wall_u[ax][sd][d] = sim->p.wall_u[ax][sd][d];
+        a.wall_omega[ax][sd][d] = sim->p.wall_omega[ax][sd][d];
+      }
+  const int threads = 128;
+  const int64_t blocks = (a.nrec + threads - 1) / threads;
+  if (sim->p.precision == VLB_F64)
+    k_pack_coef<Q, double><<<(unsigned)blocks, threads, 0, s>>>(a, (double *)sim->d_coef);
+  else
+    k_pack_coef<Q, float><<<(unsigned)blocks, threads, 0, s>>>(a, (float *)sim->d_coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_coef(const vlb_sim *sim, cudaStream_t s) {
+  return sim->mesh->md.q == 9 ? pack_q<9>(sim, s) : pack_q<19>(sim, s);
+}
+
+// ------------------------------------------------------------------ initial state
+// N_a = J f^eq_a(rho, U, U~ = U), U^i = u . g^i (Eqs. 14, 33), normal layout
+template <int Q, typename S>
+__global__ void k_init(const double *J, const double *gu, const double *ginv, const double *rho,
+                       const double *u, int64_t ncell, double nref, S *f) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  double U[D], gi[NS];
+  for (int i = 0; i < D; i++) {
+    double s = 0.0;
+    for (int d = 0; d < D; d++) s += u[c * D + d] * gu[(c * D + i) * D + d];
+    U[i] = s;
+  }
+  for (int i = 0; i < NS; i++) gi[i] = ginv[c * NS + i];
+  EqParts<Q, double> e;
+  eq_parts<Q, double>(gi, U, U, e);
+  const double r = rho[c], Jc = J[c];
+  // stored as N_a - w_a n_ref
+  f[c] = static_cast<S>(Jc * r * lat_w<Q, double>(0) * eq_even<Q, double>(e, 0) -
+                        lat_w<Q, double>(0) * nref);
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    const double E = eq_even<Q, double>(e, p), O = eq_odd<Q, double>(e, U, p);
+    const double w = lat_w<Q, double>(p), rw = Jc * r * w;
+    f[p * ncell + c] = static_cast<S>(rw * (E + O) - w * nref);
+    f[(p + H) * ncell + c] = static_cast<S>(rw * (E - O) - w * nref);
+  }
+}
+
+cudaError_t launch_init(const vlb_sim *sim, const double *d_rho, const double *d_u, cudaStream_t s) {
+  const vlb_mesh *m = sim->mesh;
+  const int threads = 128;
+  const int64_t blocks = (m->ncell + threads - 1) / threads;
+  const bool f64 = sim->p.precision == VLB_F64;
+  if (m->md.q == 9) {
+    if (f64)
+      k_init<9, double><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u,
+                                                             m->ncell, sim->nref, (double *)sim->d_f);
+    else
+      k_init<9, float><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u,
+                                                            m->ncell, sim->nref, (float *)sim->d_f);
+  } else {
+    if (f64)
+      k_init<19, double><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho,
+                                                              d_u, m->ncell, sim->nref, (double *)sim->d_f);
+    else
+      k_init<19, float><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u,
+                                                             m->ncell, sim->nref, (float *)sim->d_f);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vlb

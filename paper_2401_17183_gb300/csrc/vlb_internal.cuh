@@ -1,0 +1,323 @@
+// vlb_internal.cuh -- shared internals of libvlb (device lattice tables, the
+// per-cell collision of section 2.2, mesh/simulation objects and launcher
+// declarations). Not part of the public C-ABI (include/vlb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vlb.h"
+
+namespace vlb {
+
+// --------------------------------------------------------------------------
+// Velocity sets. Section 2.1 lists D3Q19 {0, +-e_i, +-e_i +-e_j}; D2Q9 is its
+// planar restriction. The library orders each set so that the opposite of
+// direction a (1 <= a <= H) is a + H, which lets every kernel treat the
+// (a, abar) pair as one unit.
+//   D2Q9 : 1 (1,0) 2 (0,1) 3 (1,1) 4 (-1,1)           and their negatives
+//   D3Q19: 1 (1,0,0) 2 (0,1,0) 3 (0,0,1) 4 (1,1,0) 5 (1,-1,0) 6 (1,0,1)
+//          7 (1,0,-1) 8 (0,1,1) 9 (0,1,-1)             and their negatives
+// Weights: the standard ones with T0 = 1/3 (they meet Eq. 10 to 4th order).
+template <int Q>
+struct Lat;
+
+template <>
+struct Lat<9> {
+  static constexpr int D = 2, H = 4;
+  // positive half, a = 1..4
+  __host__ __device__ static constexpr int cpos(int a, int d) {
+    return d == 0 ? (a == 1 || a == 3 ? 1 : a == 4 ? -1 : 0) : d == 1 ? (a == 1 ? 0 : 1) : 0;
+  }
+  __host__ __device__ static constexpr int c(int a, int d) {
+    return a == 0 ? 0 : a <= H ? cpos(a, d) : -cpos(a - H, d);
+  }
+};
+
+template <>
+struct Lat<19> {
+  static constexpr int D = 3, H = 9;
+  // positive half, a = 1..9
+  __host__ __device__ static constexpr int cpos(int a, int d) {
+    return d == 0   ? (a == 1 || a == 4 || a == 5 || a == 6 || a == 7 ? 1 : 0)
+           : d == 1 ? (a == 2 || a == 4 || a == 8 || a == 9 ? 1 : a == 5 ? -1 : 0)
+                    : (a == 3 || a == 6 || a == 8 ? 1 : a == 7 || a == 9 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int c(int a, int d) {
+    return a == 0 ? 0 : a <= H ? cpos(a, d) : -cpos(a - H, d);
+  }
+};
+
+template <int Q>
+__host__ __device__ constexpr int lat_nnz(int a) {
+  return (Lat<Q>::c(a, 0) != 0) + (Lat<Q>::c(a, 1) != 0) + (Lat<Q>::c(a, 2) != 0);
+}
+
+template <int Q, typename R>
+__host__ __device__ constexpr R lat_w(int a) {
+  return Q == 9 ? (a == 0 ? R(4) / R(9) : lat_nnz<Q>(a) == 1 ? R(1) / R(9) : R(1) / R(36))
+                : (a == 0 ? R(1) / R(3) : lat_nnz<Q>(a) == 1 ? R(1) / R(18) : R(1) / R(36));
+}
+
+template <int Q>
+__host__ __device__ constexpr int lat_opp(int a) {
+  return a == 0 ? 0 : (a <= Lat<Q>::H ? a + Lat<Q>::H : a - Lat<Q>::H);
+}
+
+// index of the symmetric pair (i, j) in a packed D(D+1)/2 array
+template <int D>
+__host__ __device__ constexpr int sym(int i, int j) {
+  return D == 2 ? i + j : (i < j ? i : j) == 0 ? (i > j ? i : j) : (i < j ? i : j) == 1 ? 2 + (i > j ? i : j) : 5;
+}
+
+// --------------------------------------------------------------------------
+// Coefficient record of one cell (or one column in plane mode), structure of
+// arrays: value k of record r lives at coef[k * stride + r].
+template <int Q>
+struct CoefLayout {
+  static constexpr int D = Lat<Q>::D;
+  static constexpr int NS = D * (D + 1) / 2;
+  static constexpr int J = 0;                  // J (Eq. 5)
+  static constexpr int GINV = 1;               // g^ij packed (Eq. 8)
+  static constexpr int BODY = GINV + NS;       // G^i = G . g^i
+  static constexpr int K = BODY + D;           // K^i_a, a = 1..Q-1: K + (a-1)*D + i
+  static constexpr int KW = K + (Q - 1) * D;   // sum_a w_a K^i_a (reference-state part of J F)
+  static constexpr int HM = KW + D;            // chord matrix (I - L)^-1, row-major D x D
+  static constexpr int FR = HM + D * D;        // F of the rest state at rho = 1 (start value)
+  static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
+  static constexpr int NC = UW + D;
+};
+
+// Per-cell coefficients held in registers during a collision.
+template <int Q, typename R>
+struct CellCoef {
+  static constexpr int D = Lat<Q>::D;
+  R J;
+  R gi[D * (D + 1) / 2];
+  R G[D];
+  R K[Q][D];   // K[0] = 0
+  R Kw[D];
+  R Hm[D][D];
+  R Fr[D];
+};
+
+constexpr double kT0 = 1.0 / 3.0;
+
+// max that propagates NaN from either side (a NaN residual never converges)
+template <typename R>
+__device__ __forceinline__ R maxnan(R a, R b) {
+  return (a > b || a != a) ? a : b;
+}
+__device__ __forceinline__ float absr(float x) { return fabsf(x); }
+__device__ __forceinline__ double absr(double x) { return fabs(x); }
+
+// --------------------------------------------------------------------------
+// Equilibrium of Eq. 33 for one cell, specialised to velocity sets whose
+// components are in {-1, 0, 1}. With
+//   B^ij  = (g^ij - delta^ij) T0 + U~^i U~^j,
+//   C^ijk = T0 [(g^ij U~^k - delta^ij U^k) + cyclic] + U~^i U~^j U~^k,
+//   v^i   = sum_j C^ijj,
+// the bracket of Eq. 33 is
+//   1 + c.U/T0 + (c.B.c/T0 - tr B)/(2 T0) + (C[c,c,c] - 3 T0 c.v)/(6 T0^3),
+// and C[c,c,c] only needs C^iii and C^iij for velocities with at most two
+// non-zero components. The struct holds the direction-independent parts.
+template <int Q, typename R>
+struct EqParts {
+  static constexpr int D = Lat<Q>::D;
+  R B[D][D];
+  R trB;
+  R C3[D];      // C^iii
+  R C2[D][D];   // C2[i][j] = C^iij, i != j
+  R v[D];       // v^i = sum_j C^ijj
+};
+
+template <int Q, typename R>
+__device__ __forceinline__ void eq_parts(const R (&gi)[Lat<Q>::D * (Lat<Q>::D + 1) / 2],
+                                         const R (&U)[Lat<Q>::D], const R (&Ut)[Lat<Q>::D],
+                                         EqParts<Q, R> &e) {
+  constexpr int D = Lat<Q>::D;
+  const R T0 = R(kT0);
+  e.trB = R(0);
+#pragma unroll
+  for (int i = 0; i < D; i++)
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      e.B[i][j] = (gi[sym<D>(i, j)] - (i == j ? R(1) : R(0))) * T0 + Ut[i] * Ut[j];
+    }
+#pragma unroll
+  for (int i = 0; i < D; i++) e.trB += e.B[i][i];
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    // 3 T0 = 1
+    e.C3[i] = (gi[sym<D>(i, i)] * Ut[i] - U[i]) + Ut[i] * Ut[i] * Ut[i];
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      if (i == j) continue;
+      // C^iij = T0 [(g^ii U~^j - U^j) + 2 g^ij U~^i] + U~^i U~^i U~^j
+      e.C2[i][j] = T0 * ((gi[sym<D>(i, i)] * Ut[j] - U[j]) + R(2) * gi[sym<D>(i, j)] * Ut[i]) +
+                   Ut[i] * Ut[i] * Ut[j];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    R s = e.C3[i];
+#pragma unroll
+    for (int j = 0; j < D; j++)
+      if (j != i) s += e.C2[j][i];  // C^ijj = C^jji
+    e.v[i] = s;
+  }
+}
+
+// even part of the bracket of Eq. 33 (terms with an even power of c) for
+// direction a. Called inside fully unrolled loops, so a and every c(a, i) are
+// compile-time constants and the zero terms fold away.
+template <int Q, typename R>
+__device__ __forceinline__ R eq_even(const EqParts<Q, R> &e, int a) {
+  constexpr int D = Lat<Q>::D;
+  R cbc = R(0);
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    const int ci = Lat<Q>::c(a, i);
+    if (ci == 0) continue;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      const int cj = Lat<Q>::c(a, j);
+      if (cj == 0) continue;
+      if (ci * cj > 0)
+        cbc += e.B[i][j];
+      else
+        cbc -= e.B[i][j];
+    }
+  }
+  return R(1) + (R(3) * cbc - e.trB) * R(1.5);
+}
+
+// the same even part minus its leading 1: kept separate so that the large
+// constant never goes through a rounding together with the small terms
+template <int Q, typename R>
+__device__ __forceinline__ R eq_even_dev(const EqParts<Q, R> &e, int a) {
+  constexpr int D = Lat<Q>::D;
+  R cbc = R(0);
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    const int ci = Lat<Q>::c(a, i);
+    if (ci == 0) continue;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      const int cj = Lat<Q>::c(a, j);
+      if (cj == 0) continue;
+      if (ci * cj > 0)
+        cbc += e.B[i][j];
+      else
+        cbc -= e.B[i][j];
+    }
+  }
+  return (R(3) * cbc - e.trB) * R(1.5);  // (c.B.c / T0 - tr B) / (2 T0)
+}
+
+// odd part of the bracket of Eq. 33 for direction a
+template <int Q, typename R>
+__device__ __forceinline__ R eq_odd(const EqParts<Q, R> &e, const R (&U)[Lat<Q>::D], int a) {
+  constexpr int D = Lat<Q>::D;
+  R cu = R(0), cv = R(0), ccc = R(0);
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    const int ci = Lat<Q>::c(a, i);
+    if (ci == 0) continue;
+    if (ci > 0) {
+      cu += U[i];
+      cv += e.v[i];
+      ccc += e.C3[i];
+    } else {
+      cu -= U[i];
+      cv -= e.v[i];
+      ccc -= e.C3[i];
+    }
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      const int cj = Lat<Q>::c(a, j);
+      // orderings (i,i,j), (i,j,i), (j,i,i): 3 c_i c_i c_j C^iij = 3 c_j C^iij
+      if (j == i || cj == 0) continue;
+      if (cj > 0)
+        ccc += R(3) * e.C2[i][j];
+      else
+        ccc -= R(3) * e.C2[i][j];
+    }
+  }
+  // c.U / T0 + (C[c,c,c] - 3 T0 c.v) / (6 T0^3), with 3 T0 = 1 and 1/(6 T0^3) = 9/2
+  return R(3) * cu + R(4.5) * (ccc - cv);
+}
+
+// --------------------------------------------------------------------------
+// Mesh and simulation objects (host side).
+struct MeshDev {
+  int32_t dim;
+  int32_t q;
+  int64_t n[3];
+  int32_t bc[3];
+  double shift[3][3];
+  double rot[3][9];
+  int32_t has_rot[3];
+  double dx;
+  int32_t wall_links;  // VLB_WALL_LINKS_ZERO or VLB_WALL_LINKS_GHOST
+  const double *x;     // device positions
+};
+
+}  // namespace vlb
+
+struct vlb_mesh {
+  vlb::MeshDev md;
+  int64_t ncell;
+  double *d_x = nullptr;
+  double *d_J = nullptr;     // [ncell]
+  double *d_gl = nullptr;    // [ncell][dim][dim]
+  double *d_gu = nullptr;    // [ncell][dim][dim]
+  double *d_ginv = nullptr;  // [ncell][NS]
+  double *d_K = nullptr;     // [ncell][q][dim]
+  vlb_mesh_stats stats;
+  int device = 0;
+};
+
+struct vlb_sim {
+  const vlb_mesh *mesh = nullptr;
+  vlb_params p;
+  cudaStream_t stream = nullptr;
+  void *d_f = nullptr;        // populations [q][ncell]
+  void *d_coef = nullptr;     // coefficient records [NC][ncoef]
+  int64_t ncoef = 0;
+  int32_t nc = 0;
+  int32_t plane = 0;
+  int64_t t = 0;
+  double nref = 0.0;          // populations are stored as N_a - w_a nref, nref = rho_0 J_ref
+  int *d_err = nullptr;       // sticky kernel error flags
+  double *d_fields = nullptr; // moments output staging [ncell][1 + 2 dim]
+  double *d_partial = nullptr;
+  double *d_totals = nullptr;
+  int64_t partial_blocks = 0;
+  double *d_io = nullptr;     // host<->device staging for init/state, grown on demand
+  size_t io_bytes = 0;
+};
+
+namespace vlb {
+
+// error flags raised by kernels
+enum : int { ERR_NOCONV = 1, ERR_NONFINITE = 2, ERR_GEOM = 4 };
+
+// launchers (each returns a cudaError_t from the launch)
+cudaError_t launch_geometry(const vlb_mesh *m, int *d_err, cudaStream_t s);
+cudaError_t launch_mesh_stats(const vlb_mesh *m, double *d_partial, int64_t nblk, cudaStream_t s);
+cudaError_t launch_plane_check(const vlb_mesh *m, int *d_flag, cudaStream_t s);
+cudaError_t launch_pack_coef(const vlb_sim *sim, cudaStream_t s);
+cudaError_t launch_init(const vlb_sim *sim, const double *d_rho, const double *d_u, cudaStream_t s);
+cudaError_t launch_step(const vlb_sim *sim, int odd, cudaStream_t s);
+cudaError_t launch_moments(const vlb_sim *sim, double *d_out, double *d_partial, int64_t nblk,
+                           cudaStream_t s);
+cudaError_t launch_finish_totals(const double *d_partial, int64_t nblk, double *d_totals,
+                                 cudaStream_t s);
+cudaError_t launch_get_state(const vlb_sim *sim, double *d_N, cudaStream_t s);
+cudaError_t launch_set_state(const vlb_sim *sim, const double *d_N, cudaStream_t s);
+
+constexpr int kMomThreads = 256;
+constexpr int kStatThreads = 256;
+
+}  // namespace vlb

@@ -1,0 +1,262 @@
+// vlb_moments.cu -- output mapping of Eq. 34 (rho, u = U^i g_i and
+// u~ = U~^i g_i), FP64 conservation sums (mass, P = sum e_a N_a and the
+// invariant M = sum 1/2 [e_a(q) + e_a(q - c_a)] N_a) reduced with warp
+// shuffles, and the population gather/scatter used for checkpoints.
+#include "vlb_addr.cuh"
+#include "vlb_collide.cuh"
+
+namespace vlb {
+
+struct MomArgs {
+  const void *f;
+  Grid g;
+  int64_t ncell;
+  const double *J, *gl, *gu, *ginv, *K;
+  double body[3];
+  double rot[3][9];
+  int32_t has_rot[3];
+  int32_t periodic[3];
+  double tau;
+  double nref;
+  int *err;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block sum of NV values into out[0..NV) (thread 0 writes)
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
+  __shared__ double sh[NV][kMomThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    const double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      double s = lane < (int)(blockDim.x >> 5) ? sh[k][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) out[k] = s;
+    }
+  }
+}
+
+template <int Q, typename S, bool ODD>
+__global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double *out,
+                                                         double *partial) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2;
+  const S *f = static_cast<const S *>(a.f);
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const Addr<Q> ad(a.g, c);
+    double N[Q];
+    pull<Q, ODD, S, double>(f, a.ncell, ad, N);
+#pragma unroll
+    for (int av = 0; av < Q; av++) N[av] += lat_w<Q, double>(av) * a.nref;
+    CellCoef<Q, double> k;
+    k.J = a.J[c];
+    for (int i = 0; i < NS; i++) k.gi[i] = a.ginv[c * NS + i];
+    for (int i = 0; i < D; i++) {
+      double s = 0.0;
+      for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
+      k.G[i] = s;
+      k.Kw[i] = 0.0;
+      k.Fr[i] = 0.0;
+      for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
+    }
+    for (int av = 0; av < Q; av++)
+      for (int i = 0; i < D; i++) k.K[av][i] = a.K[(c * Q + av) * D + i];
+    double Np[Q];
+    CollideState<Q, double> st;
+    // plain fixed point from F = 0 on the full populations (n_ref = 0)
+    collide_cell<Q, double, false, false>(N, k, 0.0, a.tau, 1e-14, 200, Np, st);
+    if (!st.conv) atomicOr(a.err, ERR_NOCONV);
+    double gl[D][D];
+    for (int i = 0; i < D; i++)
+      for (int d = 0; d < D; d++) gl[i][d] = a.gl[(c * D + i) * D + d];
+    double *o = out + c * (1 + 2 * D);
+    o[0] = st.rho;
+    bool finite = isfinite(st.rho);
+    for (int d = 0; d < D; d++) {
+      double uu = 0.0, ut = 0.0;
+      for (int i = 0; i < D; i++) {
+        uu += st.U[i] * gl[i][d];                                   // u = U^i g_i (Eq. 34)
+        ut += (st.U[i] + 0.5 * (st.F[i] / st.rho)) * gl[i][d];      // u~ = U~^i g_i
+      }
+      o[1 + d] = uu;
+      o[1 + D + d] = ut;
+      finite = finite && isfinite(uu) && isfinite(ut);
+    }
+    if (!finite) atomicOr(a.err, ERR_NONFINITE);
+    // conservation sums
+#pragma unroll 1
+    for (int av = 0; av < Q; av++) {
+      acc[0] += N[av];
+      double e[D], eb[D];
+      for (int d = 0; d < D; d++) {
+        double s = 0.0;
+        for (int i = 0; i < D; i++) s += Lat<Q>::c(av, i) * gl[i][d];
+        e[d] = s;
+        eb[d] = s;
+      }
+      if (av != 0 && !ad.crosses(av, -1)) {
+        // e_a at q - c_a: tangents of the wrapped neighbour, rotated back if the
+        // step crosses a periodic seam that carries a rotation
+        const int64_t nb = ad.nb(av, -1);
+        double gn[D][D];
+        for (int i = 0; i < D; i++)
+          for (int d = 0; d < D; d++) gn[i][d] = a.gl[(nb * D + i) * D + d];
+        for (int ax = 0; ax < D; ax++) {
+          const int cax = Lat<Q>::c(av, ax);
+          if (!a.has_rot[ax] || !a.periodic[ax] || cax == 0) continue;
+          const bool below = (cax > 0 && ad.ic[ax] == 0);             // image at index -1: R^T
+          const bool above = (cax < 0 && ad.ic[ax] == a.g.n[ax] - 1);  // image at index n: R
+          if (!below && !above) continue;
+          const double *R = a.rot[ax];
+          for (int i = 0; i < D; i++) {
+            double y[D];
+            for (int r = 0; r < D; r++) {
+              double s = 0.0;
+              for (int cc = 0; cc < D; cc++) s += (above ? R[3 * r + cc] : R[3 * cc + r]) * gn[i][cc];
+              y[r] = s;
+            }
+            for (int r = 0; r < D; r++) gn[i][r] = y[r];
+          }
+        }
+        for (int d = 0; d < D; d++) {
+          double s = 0.0;
+          for (int i = 0; i < D; i++) s += Lat<Q>::c(av, i) * gn[i][d];
+          eb[d] = s;
+        }
+      }
+      for (int d = 0; d < D; d++) {
+        acc[1 + d] += e[d] * N[av];
+        acc[4 + d] += 0.5 * (e[d] + eb[d]) * N[av];
+      }
+    }
+  }
+  block_sum<7>(acc, partial + (int64_t)blockIdx.x * 7);
+}
+
+template <int Q, typename S>
+static cudaError_t moments_t(const vlb_sim *sim, double *d_out, double *d_partial, int64_t nblk,
+                             cudaStream_t s) {
+  const vlb_mesh *m = sim->mesh;
+  MomArgs a;
+  a.f = sim->d_f;
+  a.g = make_grid(m);
+  a.ncell = m->ncell;
+  a.J = m->d_J;
+  a.gl = m->d_gl;
+  a.gu = m->d_gu;
+  a.ginv = m->d_ginv;
+  a.K = m->d_K;
+  for (int d = 0; d < 3; d++) {
+    a.body[d] = sim->p.body_force[d];
+    a.has_rot[d] = m->md.has_rot[d];
+    a.periodic[d] = (d < m->md.dim && m->md.bc[d] == VLB_PERIODIC) ? 1 : 0;
+    for (int k = 0; k < 9; k++) a.rot[d][k] = m->md.rot[d][k];
+  }
+  a.tau = sim->p.tau;
+  a.nref = sim->nref;
+  a.err = sim->d_err;
+  if (sim->t & 1)
+    k_moments<Q, S, true><<<(unsigned)nblk, kMomThreads, 0, s>>>(a, d_out, d_partial);
+  else
+    k_moments<Q, S, false><<<(unsigned)nblk, kMomThreads, 0, s>>>(a, d_out, d_partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const vlb_sim *sim, double *d_out, double *d_partial, int64_t nblk,
+                           cudaStream_t s) {
+  const bool f64 = sim->p.precision == VLB_F64;
+  if (sim->mesh->md.q == 9)
+    return f64 ? moments_t<9, double>(sim, d_out, d_partial, nblk, s)
+               : moments_t<9, float>(sim, d_out, d_partial, nblk, s);
+  return f64 ? moments_t<19, double>(sim, d_out, d_partial, nblk, s)
+             : moments_t<19, float>(sim, d_out, d_partial, nblk, s);
+}
+
+// fixed-order reduction of the per-block partial sums (deterministic)
+__global__ void __launch_bounds__(kMomThreads) k_finish_totals(const double *partial, int64_t nblk,
+                                                               double *totals) {
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int k = 0; k < 7; k++) v[k] += partial[b * 7 + k];
+  block_sum<7>(v, totals);
+}
+
+cudaError_t launch_finish_totals(const double *d_partial, int64_t nblk, double *d_totals,
+                                 cudaStream_t s) {
+  k_finish_totals<<<1, kMomThreads, 0, s>>>(d_partial, nblk, d_totals);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ state gather / scatter
+template <int Q, typename S, bool ODD>
+__global__ void k_get_state(const S *f, Grid g, int64_t ncell, double nref, double *N_out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const Addr<Q> ad(g, c);
+  double N[Q];
+  pull<Q, ODD, S, double>(f, ncell, ad, N);
+#pragma unroll
+  for (int a = 0; a < Q; a++) N_out[a * ncell + c] = N[a] + lat_w<Q, double>(a) * nref;
+}
+
+template <int Q, typename S>
+__global__ void k_set_state(S *f, int64_t ncell, double nref, const double *N_in) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+#pragma unroll
+  for (int a = 0; a < Q; a++)
+    f[a * ncell + c] = static_cast<S>(N_in[a * ncell + c] - lat_w<Q, double>(a) * nref);
+}
+
+template <int Q, typename S>
+static cudaError_t get_t(const vlb_sim *sim, double *d_N, cudaStream_t s) {
+  const vlb_mesh *m = sim->mesh;
+  const int threads = 256;
+  const int64_t blocks = (m->ncell + threads - 1) / threads;
+  const Grid g = make_grid(m);
+  if (sim->t & 1)
+    k_get_state<Q, S, true><<<(unsigned)blocks, threads, 0, s>>>((const S *)sim->d_f, g, m->ncell, sim->nref, d_N);
+  else
+    k_get_state<Q, S, false><<<(unsigned)blocks, threads, 0, s>>>((const S *)sim->d_f, g, m->ncell, sim->nref, d_N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const vlb_sim *sim, double *d_N, cudaStream_t s) {
+  const bool f64 = sim->p.precision == VLB_F64;
+  if (sim->mesh->md.q == 9) return f64 ? get_t<9, double>(sim, d_N, s) : get_t<9, float>(sim, d_N, s);
+  return f64 ? get_t<19, double>(sim, d_N, s) : get_t<19, float>(sim, d_N, s);
+}
+
+cudaError_t launch_set_state(const vlb_sim *sim, const double *d_N, cudaStream_t s) {
+  const vlb_mesh *m = sim->mesh;
+  const int threads = 256;
+  const int64_t blocks = (m->ncell + threads - 1) / threads;
+  const bool f64 = sim->p.precision == VLB_F64;
+  if (m->md.q == 9) {
+    if (f64)
+      k_set_state<9, double><<<(unsigned)blocks, threads, 0, s>>>((double *)sim->d_f, m->ncell, sim->nref, d_N);
+    else
+      k_set_state<9, float><<<(unsigned)blocks, threads, 0, s>>>((float *)sim->d_f, m->ncell, sim->nref, d_N);
+  } else {
+    if (f64)
+      k_set_state<19, double><<<(unsigned)blocks, threads, 0, s>>>((double *)sim->d_f, m->ncell, sim->nref, d_N);
+    else
+      k_set_state<19, float><<<(unsigned)blocks, threads, 0, s>>>((float *)sim->d_f, m->ncell, sim->nref, d_N);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vlb

@@ -14,6 +14,7 @@ A mesh is a plain dict:
   shift, rot   periodic image across the +end of axis a is rot[a] @ x + shift[a]
                (rot[a] row-major 3x3; all zeros means identity)
   dx           representative spacing of Eq. 3
+  wall_links   Theta on wall-crossing links: 0 zero, 1 from the ghost nodes
 """
 import math
 
@@ -44,7 +45,7 @@ def uniform(seed, ncell, ncomp):
     return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
-def _mesh(dim, n, x, bc, shift=None, rot=None, dx=1.0):
+def _mesh(dim, n, x, bc, shift=None, rot=None, dx=1.0, wall_links=0):
     n3 = (int(n[0]), int(n[1]), int(n[2]) if dim == 3 else 1)
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(n3 + (dim,)))
     sh = np.zeros((3, 3))
@@ -57,7 +58,7 @@ def _mesh(dim, n, x, bc, shift=None, rot=None, dx=1.0):
         rt[:r.shape[0], :r.shape[1]] = r
     bc3 = [int(b) for b in bc] + [PERIODIC] * (3 - len(bc))
     return {"dim": dim, "q": 9 if dim == 2 else 19, "n": n3, "x": x, "bc": tuple(bc3),
-            "shift": sh, "rot": rt, "dx": float(dx)}
+            "shift": sh, "rot": rt, "dx": float(dx), "wall_links": int(wall_links)}
 
 
 def ncell(mesh):
@@ -96,7 +97,7 @@ def affine_mesh(A, n, b=None, dim=None):
     return _mesh(dim, n3, X, [PERIODIC] * dim, shift=shift)
 
 
-def channel_mesh(n0=256, n1=256, n2=256, stretch=2.5, bump=0.05):
+def channel_mesh(n0=256, n1=256, n2=256, stretch=2.5, bump=0.05, wall_links=0):
     """3D channel with a bumped lower wall, in lattice units.
 
     Axis 0 (xi) streamwise and periodic, axis 1 (eta) wall-normal with walls,
@@ -119,10 +120,10 @@ def channel_mesh(n0=256, n1=256, n2=256, stretch=2.5, bump=0.05):
     X[..., 1] = y[:, :, None]
     X[..., 2] = np.arange(n2, dtype=np.float64)[None, None, :]
     return _mesh(3, (n0, n1, n2), X, (PERIODIC, WALL, PERIODIC),
-                 shift=[[n0, 0, 0], [0, 0, 0], [0, 0, n2]])
+                 shift=[[n0, 0, 0], [0, 0, 0], [0, 0, n2]], wall_links=wall_links)
 
 
-def polar_mesh(nr, ntheta, r_in, r_out, dtheta=None):
+def polar_mesh(nr, ntheta, r_in, r_out, dtheta=None, wall_links=0):
     """2D annular sector: r_i = r_in + (i + 1/2) dr (walls at r_in, r_out),
     theta_j = j dtheta, periodic in theta through a rotation by ntheta dtheta."""
     dr = (r_out - r_in) / nr
@@ -134,7 +135,7 @@ def polar_mesh(nr, ntheta, r_in, r_out, dtheta=None):
     X = np.stack([R * np.cos(T), R * np.sin(T)], axis=-1)[:, :, None, :]
     ang = ntheta * dtheta
     rot = [[0] * 9, [math.cos(ang), -math.sin(ang), 0, math.sin(ang), math.cos(ang), 0, 0, 0, 1]]
-    return _mesh(2, (nr, ntheta, 1), X, (WALL, PERIODIC), rot=rot)
+    return _mesh(2, (nr, ntheta, 1), X, (WALL, PERIODIC), rot=rot, wall_links=wall_links)
 
 
 def polar_periodic_mesh(nr, ntheta, r0, dr, dtheta):
