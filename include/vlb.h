@@ -188,6 +188,26 @@ int vlb_sim_layout(const vlb_sim *sim, int32_t *coef_per_cell, int32_t *plane_mo
 void vlb_destroy(vlb_sim *sim);
 const char *vlb_last_error(void);
 
+/* The paper has no counterpart to this call: it is a service for callers that
+ * cannot allocate device memory -- code whose device memory comes from a fixed
+ * budget or from a pool allocator it does not own, and latency-bound
+ * monitoring loops in which an allocation, which can synchronise the device,
+ * is not acceptable. vlb_moments allocates its staging buffers on first use;
+ * this call computes the same totals[7] (mass, P, M) and allocates nothing.
+ *   d_totals  DEVICE pointer to 7 doubles owned by the caller, written
+ *             asynchronously on the simulation's stream (layout as in
+ *             vlb_moments; unused components of 2D runs are zero).
+ * Its per-block partial sums live in a fixed device array of 4096 x 7 doubles
+ * (224 KiB) that every device which loads the library holds until the process
+ * exits; meshes of more than 4096 x 16384 = 67,108,864 cells are rejected
+ * with VLB_EINVAL. The first call on a device looks up that array's device
+ * address; make the first call before any stream capture. All calls share the
+ * array, so calls that overlap on the GPU (for example on two streams) race
+ * and give wrong totals; every call writes each slot it reads before reading
+ * it, so nothing needs clearing. Errors: VLB_EINVAL, VLB_ECUDA. Kernel-raised
+ * errors are not checked here (no synchronisation). */
+int vlb_totals_noalloc(vlb_sim *sim, double *d_totals);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,14 @@ int ensure_io(vlb_sim *s, size_t bytes) {
 
 }  // namespace
 
+int vlb::set_error(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
 extern "C" {
 
 const char *vlb_last_error(void) { return g_err; }

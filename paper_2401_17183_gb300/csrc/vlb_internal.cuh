@@ -317,6 +317,9 @@ cudaError_t launch_finish_totals(const double *d_partial, int64_t nblk, double *
 cudaError_t launch_get_state(const vlb_sim *sim, double *d_N, cudaStream_t s);
 cudaError_t launch_set_state(const vlb_sim *sim, const double *d_N, cudaStream_t s);
 
+// records a thread-local error message for vlb_last_error() and returns code
+int set_error(int code, const char *fmt, ...);
+
 constexpr int kMomThreads = 256;
 constexpr int kStatThreads = 256;
 

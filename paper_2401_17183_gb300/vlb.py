@@ -80,6 +80,7 @@ def load():
                             C.POINTER(C.c_int64)], C.c_int),
         "vlb_destroy": ([vp], None),
         "vlb_last_error": ([], C.c_char_p),
+        "vlb_totals_noalloc": ([vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +234,10 @@ class Sim:
         cast = lambda p: C.cast(p, _DP) if p else None  # noqa: E731
         _check(load().vlb_moments(self.h, cast(rho_ptr), cast(u_ptr), cast(ut_ptr),
                                   cast(tot_ptr)), "vlb_moments")
+
+    def totals_noalloc(self, d_totals_ptr):
+        """vlb_totals_noalloc into 7 doubles of caller-owned device memory."""
+        _check(load().vlb_totals_noalloc(self.h, C.c_void_p(d_totals_ptr)), "vlb_totals_noalloc")
 
     def get_state(self):
         N = np.zeros((self.mesh.q, self.mesh.ncell))
