@@ -2,10 +2,13 @@
 """Throughput of the fused volumetric-curvilinear stream-and-collide step.
 
 Workload: D3Q19, 256^3 cells, FP32 populations, a channel with tanh wall-normal
-stretching and a sinusoidal bump on the lower wall (amplitude 0.05 h,
-wavelength half the streamwise length), walls with halfway bounce-back,
-periodic streamwise and spanwise axes, constant body force, tau = 0.6, rho = 1
-with seeded 1% velocity noise. A step is one time step over the whole lattice
+stretching (factor 0.7) and a sinusoidal bump on the lower wall (amplitude
+0.05 h, wavelength half the streamwise length), walls with halfway
+bounce-back, periodic streamwise and spanwise axes, constant body force,
+tau = 0.8, rho = 1 with seeded 1% velocity noise. (Stretching 2.5 makes the
+rest equilibrium negative near the walls and the run fails within tens of
+steps; at tau <= 0.6 this bumped mesh is unstable at the lower wall after
+about 300 steps. The per-cell work does not depend on either value.) A step is one time step over the whole lattice
 (one fused kernel launch). Metric: MLUPS (million cell updates per second) and
 the fraction of the measured HBM copy bandwidth that the algorithmic traffic
 (each population read and written once, 2 * 19 * 4 = 152 bytes per cell
@@ -43,6 +46,8 @@ def args_parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=256, help="cells per axis")
     ap.add_argument("--stretch", type=float, default=0.7)
+    ap.add_argument("--bump", type=float, default=0.05)
+    ap.add_argument("--tau", type=float, default=0.8)
     ap.add_argument("--coef-mode", default="auto", choices=["auto", "full", "plane"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -139,14 +144,14 @@ def cpu_model():
     return os.uname().machine
 
 
-def reference_sample_run(steps, warmup, budget_s=120.0):
+def reference_sample_run(steps, warmup, tau, stretch, bump, budget_s=120.0):
     """The FP64 oracle on the host cores, on a bounded sample of the channel family."""
     from oracle import OracleSim
     from paper_2401_17183_gb300 import workloads as W
-    prm = W.params(0.6, body_force=(1e-6, 0.0, 0.0))
+    prm = W.params(tau, body_force=(1e-6, 0.0, 0.0))
 
     def run(s, k):
-        mesh = W.channel_mesh(s, s, s, stretch=0.7, bump=0.05)
+        mesh = W.channel_mesh(s, s, s, stretch=stretch, bump=bump)
         rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
         o = OracleSim(mesh, prm)
         o.init(rho, u)
@@ -160,7 +165,7 @@ def reference_sample_run(steps, warmup, budget_s=120.0):
     s = 4
     while (s + 2) ** 3 * per_cell <= per_step_budget and s < 32:
         s += 2
-    mesh = W.channel_mesh(s, s, s, stretch=0.7, bump=0.05)
+    mesh = W.channel_mesh(s, s, s, stretch=stretch, bump=bump)
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
     o = OracleSim(mesh, prm)
     o.init(rho, u)
@@ -169,16 +174,16 @@ def reference_sample_run(steps, warmup, budget_s=120.0):
     o.step(steps)
     el = time.perf_counter() - t
     return {"value": s ** 3 * steps / el / 1e6, "cells": s ** 3, "steps": steps, "seconds": el,
-            "sample": "%d^3 cells of the same channel family (stretch 0.7, bump 0.05 h, walls, "
-                      "body force, tau 0.6), %d timed steps" % (s, steps)}
+            "sample": "%d^3 cells of the same channel family (stretch %g, bump %g h, walls, "
+                      "body force, tau %g), %d timed steps" % (s, stretch, bump, tau, steps)}
 
 
-def cpu_baseline_leg():
+def cpu_baseline_leg(tau, stretch, bump):
     """Oracle MLUPS on a bounded sample (about 10-20 s of CPU work), 1 thread."""
     from oracle import OracleSim
     from paper_2401_17183_gb300 import workloads as W
-    prm = W.params(0.6, body_force=(1e-6, 0.0, 0.0))
-    mesh = W.channel_mesh(32, 32, 16, stretch=0.7, bump=0.05)
+    prm = W.params(tau, body_force=(1e-6, 0.0, 0.0))
+    mesh = W.channel_mesh(32, 32, 16, stretch=stretch, bump=bump)
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
     o = OracleSim(mesh, prm)
     o.init(rho, u)
@@ -192,8 +197,9 @@ def cpu_baseline_leg():
     nc = 32 * 32 * 16
     return {"value": nc * k / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "cpu": cpu_model(),
-            "sample": "32x32x16 cells of the same channel family (D3Q19, FP64, stretch 0.7, "
-                      "bump 0.05 h), %d steps, %.1f s, single thread" % (k, el)}
+            "sample": "32x32x16 cells of the same channel family (D3Q19, FP64, stretch %g, "
+                      "bump %g h, tau %g), %d steps, %.1f s, single thread"
+                      % (stretch, bump, tau, k, el)}
 
 
 def main():
@@ -203,14 +209,14 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     metric = "MLUPS & % HBM roofline (fused D3Q19 stream-and-collide step)"
     cfg = {"workload": "channel_d3q19_%d^3_fp32" % a.n, "cells": a.n ** 3, "lattice": "D3Q19",
-           "stretch": a.stretch, "bump": 0.05, "tau": 0.6, "walls": "eta (halfway bounce-back)",
+           "stretch": a.stretch, "bump": a.bump, "tau": a.tau, "walls": "eta (halfway bounce-back)",
            "periodic": "xi, zeta", "body_force": 1e-6,
            "l2": "no flush: populations %.2f GB > 129 MB L2" % (a.n ** 3 * 152 / 2 / 1e9)}
 
     if a.impl == "reference":
         if rank != 0:
             return
-        r = reference_sample_run(a.steps, a.warmup)
+        r = reference_sample_run(a.steps, a.warmup, a.tau, a.stretch, a.bump)
         line = {"impl": "reference", "metric": metric, "value": r["value"], "unit": "MLUPS",
                 "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": 1e3 * r["seconds"] / r["steps"], "higher_is_better": True,
@@ -239,8 +245,8 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    mesh = W.channel_mesh(a.n, a.n, a.n, stretch=a.stretch, bump=0.05)
-    prm = W.params(0.6, body_force=(1e-6, 0.0, 0.0))
+    mesh = W.channel_mesh(a.n, a.n, a.n, stretch=a.stretch, bump=a.bump)
+    prm = W.params(a.tau, body_force=(1e-6, 0.0, 0.0))
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
     ncell = W.ncell(mesh)
     gmesh = vlb.Mesh(mesh)
@@ -313,7 +319,7 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline_leg()
+    cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline_leg(a.tau, a.stretch, a.bump)
     line = {
         "metric": metric, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,

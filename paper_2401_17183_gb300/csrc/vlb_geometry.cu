@@ -231,11 +231,12 @@ __global__ void k_mesh_stats(const double *J, const double *ginv, int64_t ncell,
        c += (int64_t)gridDim.x * blockDim.x) {
     v[0] = fmin(v[0], J[c]);
     v[1] = fmin(v[1], -J[c]);
-    double gi[NS], U[D], Ut[D];
-    for (int i = 0; i < NS; i++) gi[i] = ginv[c * NS + i];
+    double gi[NS], gd[NS], U[D], Ut[D];
+    for (int i = 0; i < NS; i++) gd[i] = gi[i] = ginv[c * NS + i];
+    for (int i = 0; i < D; i++) gd[sym<D>(i, i)] -= 1.0;
     for (int i = 0; i < D; i++) U[i] = Ut[i] = 0.0;
     EqParts<Q, double> e;
-    eq_parts<Q, double>(gi, U, Ut, e);
+    eq_parts<Q, double>(gd, U, Ut, e);
     double m = eq_even<Q, double>(e, 0);
 #pragma unroll
     for (int p = 1; p <= H; p++) m = fmin(m, eq_even<Q, double>(e, p));
@@ -323,7 +324,7 @@ __device__ void chord_matrix(const CellCoef<Q, double> &k, double tau, double (&
   const double T0 = kT0, itau = 1.0 / tau, cpi = -0.5 * (1.0 - 0.5 * itau);
   double g[D][D], trg = 0.0;
   for (int i = 0; i < D; i++)
-    for (int j = 0; j < D; j++) g[i][j] = k.gi[sym<D>(i, j)];
+    for (int j = 0; j < D; j++) g[i][j] = k.gd[sym<D>(i, j)] + (i == j ? 1.0 : 0.0);
   for (int i = 0; i < D; i++) trg += g[i][i];
   double h[Q][D];
   for (int a = 0; a < Q; a++) {
@@ -391,7 +392,10 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
   const int64_t c = a.plane ? r * a.nfast : r;
   const int64_t st = a.stride;
   coef[L::J * st + r] = static_cast<R>(a.J[c]);
-  for (int i = 0; i < NS; i++) coef[(L::GINV + i) * st + r] = static_cast<R>(a.ginv[c * NS + i]);
+  for (int i = 0; i < D; i++)
+    for (int j = i; j < D; j++)
+      coef[(L::GINV + sym<D>(i, j)) * st + r] =
+          static_cast<R>(a.ginv[c * NS + sym<D>(i, j)] - (i == j ? 1.0 : 0.0));
   for (int i = 0; i < D; i++) {
     double s = 0.0;
     for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];  // G^i = G . g^i
@@ -404,18 +408,22 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
   for (int i = 0; i < D; i++) {
     double s = 0.0;
     for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * a.K[(c * Q + av) * D + i];
-    coef[(L::KW + i) * st + r] = static_cast<R>(s);
+    const R hi = static_cast<R>(s);
+    coef[(L::KW + i) * st + r] = hi;
+    coef[(L::KWL + i) * st + r] = static_cast<R>(s - static_cast<double>(hi));
   }
   // chord matrix and rest-state force
   {
     CellCoef<Q, double> k;
     k.J = a.J[c];
-    for (int i = 0; i < NS; i++) k.gi[i] = a.ginv[c * NS + i];
+    for (int i = 0; i < NS; i++) k.gd[i] = a.ginv[c * NS + i];
+    for (int i = 0; i < D; i++) k.gd[sym<D>(i, i)] -= 1.0;
     for (int i = 0; i < D; i++) {
       double s = 0.0;
       for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
       k.G[i] = s;
       k.Kw[i] = 0.0;
+      k.KwL[i] = 0.0;
       k.Fr[i] = 0.0;
       for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
     }
@@ -426,11 +434,10 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
     for (int i = 0; i < D; i++)
       for (int j = 0; j < D; j++) coef[(L::HM + i * D + j) * st + r] = static_cast<R>(Hm[i][j]);
     // F at rest (rho = 1, U = 0), the start value of the chord iteration
-    double N[Q], U0[D], gi[NS];
+    double N[Q], U0[D];
     for (int i = 0; i < D; i++) U0[i] = 0.0;
-    for (int i = 0; i < NS; i++) gi[i] = k.gi[i];
     EqParts<Q, double> e;
-    eq_parts<Q, double>(gi, U0, U0, e);
+    eq_parts<Q, double>(k.gd, U0, U0, e);
     for (int av = 0; av < Q; av++) {
       const int p = av <= Lat<Q>::H ? av : av - Lat<Q>::H;
       N[av] = k.J * lat_w<Q, double>(av) * eq_even<Q, double>(e, p);
@@ -510,15 +517,17 @@ __global__ void k_init(const double *J, const double *gu, const double *ginv, co
   constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
-  double U[D], gi[NS];
+  double U[D], gd[NS], zero[D];
   for (int i = 0; i < D; i++) {
     double s = 0.0;
     for (int d = 0; d < D; d++) s += u[c * D + d] * gu[(c * D + i) * D + d];
     U[i] = s;
+    zero[i] = 0.0;
   }
-  for (int i = 0; i < NS; i++) gi[i] = ginv[c * NS + i];
+  for (int i = 0; i < NS; i++) gd[i] = ginv[c * NS + i];
+  for (int i = 0; i < D; i++) gd[sym<D>(i, i)] -= 1.0;
   EqParts<Q, double> e;
-  eq_parts<Q, double>(gi, U, U, e);
+  eq_parts<Q, double>(gd, U, zero, e);
   const double r = rho[c], Jc = J[c];
   // stored as N_a - w_a n_ref
   f[c] = static_cast<S>(Jc * r * lat_w<Q, double>(0) * eq_even<Q, double>(e, 0) -

@@ -78,11 +78,12 @@ struct CoefLayout {
   static constexpr int D = Lat<Q>::D;
   static constexpr int NS = D * (D + 1) / 2;
   static constexpr int J = 0;                  // J (Eq. 5)
-  static constexpr int GINV = 1;               // g^ij packed (Eq. 8)
+  static constexpr int GINV = 1;               // g^ij - delta^ij packed (Eq. 8)
   static constexpr int BODY = GINV + NS;       // G^i = G . g^i
   static constexpr int K = BODY + D;           // K^i_a, a = 1..Q-1: K + (a-1)*D + i
   static constexpr int KW = K + (Q - 1) * D;   // sum_a w_a K^i_a (reference-state part of J F)
-  static constexpr int HM = KW + D;            // chord matrix (I - L)^-1, row-major D x D
+  static constexpr int KWL = KW + D;           // its low part: KW + KWL = the FP64 value
+  static constexpr int HM = KWL + D;           // chord matrix (I - L)^-1, row-major D x D
   static constexpr int FR = HM + D * D;        // F of the rest state at rho = 1 (start value)
   static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
   static constexpr int NC = UW + D;
@@ -93,10 +94,11 @@ template <int Q, typename R>
 struct CellCoef {
   static constexpr int D = Lat<Q>::D;
   R J;
-  R gi[D * (D + 1) / 2];
+  R gd[D * (D + 1) / 2];  // g^ij - delta^ij: stored as a deviation so that rounding is
+                          // relative to the (small) departure from a uniform lattice
   R G[D];
   R K[Q][D];   // K[0] = 0
-  R Kw[D];
+  R Kw[D], KwL[D];
   R Hm[D][D];
   R Fr[D];
 };
@@ -132,29 +134,32 @@ struct EqParts {
 };
 
 template <int Q, typename R>
-__device__ __forceinline__ void eq_parts(const R (&gi)[Lat<Q>::D * (Lat<Q>::D + 1) / 2],
-                                         const R (&U)[Lat<Q>::D], const R (&Ut)[Lat<Q>::D],
+__device__ __forceinline__ void eq_parts(const R (&gd)[Lat<Q>::D * (Lat<Q>::D + 1) / 2],
+                                         const R (&U)[Lat<Q>::D], const R (&dU)[Lat<Q>::D],
                                          EqParts<Q, R> &e) {
+  // gd = g^ij - delta^ij and U~ = U + dU; every difference of large terms is
+  // written out so that only small quantities are rounded
   constexpr int D = Lat<Q>::D;
   const R T0 = R(kT0);
+  R Ut[D];
+#pragma unroll
+  for (int i = 0; i < D; i++) Ut[i] = U[i] + dU[i];
   e.trB = R(0);
 #pragma unroll
   for (int i = 0; i < D; i++)
 #pragma unroll
-    for (int j = 0; j < D; j++) {
-      e.B[i][j] = (gi[sym<D>(i, j)] - (i == j ? R(1) : R(0))) * T0 + Ut[i] * Ut[j];
-    }
+    for (int j = 0; j < D; j++) e.B[i][j] = gd[sym<D>(i, j)] * T0 + Ut[i] * Ut[j];
 #pragma unroll
   for (int i = 0; i < D; i++) e.trB += e.B[i][i];
 #pragma unroll
   for (int i = 0; i < D; i++) {
-    // 3 T0 = 1
-    e.C3[i] = (gi[sym<D>(i, i)] * Ut[i] - U[i]) + Ut[i] * Ut[i] * Ut[i];
+    // C^iii = 3 T0 (g^ii U~^i - U^i) + (U~^i)^3, 3 T0 = 1
+    e.C3[i] = (gd[sym<D>(i, i)] * Ut[i] + dU[i]) + Ut[i] * Ut[i] * Ut[i];
 #pragma unroll
     for (int j = 0; j < D; j++) {
       if (i == j) continue;
       // C^iij = T0 [(g^ii U~^j - U^j) + 2 g^ij U~^i] + U~^i U~^i U~^j
-      e.C2[i][j] = T0 * ((gi[sym<D>(i, i)] * Ut[j] - U[j]) + R(2) * gi[sym<D>(i, j)] * Ut[i]) +
+      e.C2[i][j] = T0 * ((gd[sym<D>(i, i)] * Ut[j] + dU[j]) + R(2) * gd[sym<D>(i, j)] * Ut[i]) +
                    Ut[i] * Ut[i] * Ut[j];
     }
   }

@@ -63,12 +63,14 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
     for (int av = 0; av < Q; av++) N[av] += lat_w<Q, double>(av) * a.nref;
     CellCoef<Q, double> k;
     k.J = a.J[c];
-    for (int i = 0; i < NS; i++) k.gi[i] = a.ginv[c * NS + i];
+    for (int i = 0; i < NS; i++) k.gd[i] = a.ginv[c * NS + i];
+    for (int i = 0; i < D; i++) k.gd[sym<D>(i, i)] -= 1.0;
     for (int i = 0; i < D; i++) {
       double s = 0.0;
       for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
       k.G[i] = s;
       k.Kw[i] = 0.0;
+      k.KwL[i] = 0.0;
       k.Fr[i] = 0.0;
       for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
     }

@@ -53,11 +53,12 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs a) {
   CellCoef<Q, R> k;
   k.J = coef[L::J * cs + rec];
 #pragma unroll
-  for (int i = 0; i < L::NS; i++) k.gi[i] = coef[(L::GINV + i) * cs + rec];
+  for (int i = 0; i < L::NS; i++) k.gd[i] = coef[(L::GINV + i) * cs + rec];
 #pragma unroll
   for (int i = 0; i < D; i++) {
     k.G[i] = coef[(L::BODY + i) * cs + rec];
     k.Kw[i] = coef[(L::KW + i) * cs + rec];
+    k.KwL[i] = coef[(L::KWL + i) * cs + rec];
     k.Fr[i] = coef[(L::FR + i) * cs + rec];
     k.K[0][i] = R(0);
 #pragma unroll
@@ -82,7 +83,12 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs a) {
 #pragma unroll
   for (int i = 0; i < D; i++) uw[i] = moving ? coef[(L::UW + i) * cs + rec] : R(0);
   EqParts<Q, R> ew;
-  if (moving) eq_parts<Q, R>(k.gi, uw, uw, ew);
+  if (moving) {
+    R zero[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) zero[i] = R(0);
+    eq_parts<Q, R>(k.gd, uw, zero, ew);
+  }
 
   // ---- push (write side of Eq. 22)
 #pragma unroll
