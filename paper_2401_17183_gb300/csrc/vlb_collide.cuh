@@ -26,109 +26,166 @@ struct CollideState {
   bool conv;
 };
 
-// One evaluation of the collision for a given Phi = J F. Writes the
-// post-collision deviations dp and returns Phi_new = J F_new (Eq. 27 plus the
-// body force) in Po.
+// Direction-independent part of one collision evaluation for a given
+// Phi = J F: the equilibrium of Eq. 33 as J f^eq_a = w_a m (1 + x_a) with
+// x_p = xe_p + xo_p and x_pbar = xe_p - xo_p (only x is formed, never 1 + x),
+// and the symmetric part of deltaPi (Eq. 30) as dS[i][j] = dPi^ij + dPi^ji
+// halved, with its trace.
 //   m = sum N = n_ref + mdev,  rho = m / J,  U~ = U + Phi / (2 m)
-//   Pc = m G - 1/2 sum_a K_abar d_a - n_ref sum_a w_a K_a
 // Working with J F rather than F keeps J out of every product that is formed
 // once per step with the same operands.
 template <int Q, typename R>
-__device__ __forceinline__ void collide_eval(const R (&d)[Q], const CellCoef<Q, R> &k,
-                                             const R (&U)[Lat<Q>::D], R rho, R h2m, R m,
-                                             R mdev, const R (&Phi)[Lat<Q>::D],
-                                             const R (&Pc)[Lat<Q>::D], R itau, R cpi,
-                                             R (&dp)[Q], R (&Po)[Lat<Q>::D]) {
+struct EvalParts {
+  static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  R xe[H + 1], xo[H + 1];
+  R dP[D][D];
+  R tr;
+};
+
+template <int Q, typename R>
+__device__ __forceinline__ void eval_parts(const CellCoef<Q, R> &k, const R (&Mp)[Lat<Q>::H + 1][Lat<Q>::D],
+                                           const R (&U)[Lat<Q>::D], R rho, R h2m,
+                                           const R (&Phi)[Lat<Q>::D], R cpi,
+                                           EvalParts<Q, R> &ev) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   R dU[D];
 #pragma unroll
   for (int i = 0; i < D; i++) dU[i] = Phi[i] * h2m;
   EqParts<Q, R> e;
   eq_parts<Q, R>(k.gd, U, dU, e);
-
-  // f^eq (Eq. 33) as J f^eq_a = w_a m (1 + x_a); pair by pair x_p = xe_p + xo_p
-  // and x_pbar = xe_p - xo_p. Only x is formed, never 1 + x.
-  R xe[H + 1], xo[H + 1];
-  xe[0] = eq_even_dev<Q, R>(e, 0);
-  xo[0] = R(0);
+  ev.xe[0] = eq_even_dev<Q, R>(e, 0);
+  ev.xo[0] = R(0);
 #pragma unroll
   for (int p = 1; p <= H; p++) {
-    xe[p] = eq_even_dev<Q, R>(e, p);
-    xo[p] = eq_odd<Q, R>(e, U, p);
+    ev.xe[p] = eq_even_dev<Q, R>(e, p);
+    ev.xo[p] = eq_odd<Q, R>(e, U, p);
   }
-
   // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a - L^j_a) f^eq_a   (Eq. 30)
-  // with K_a - L_a = K_a + K_abar; a pair contributes c_p (f_p - f_pbar), and
+  // with K_a - L_a = K_a + K_abar = M_p; a pair contributes c_p (f_p - f_pbar),
   // f_p - f_pbar = 2 rho w_p xo_p
-  R dP[D][D];
 #pragma unroll
   for (int i = 0; i < D; i++)
 #pragma unroll
-    for (int j = 0; j < D; j++) dP[i][j] = R(0);
+    for (int j = 0; j < D; j++) ev.dP[i][j] = R(0);
 #pragma unroll
   for (int p = 1; p <= H; p++) {
-    const R df = R(2) * lat_w<Q, R>(p) * xo[p];
+    const R df = R(2) * lat_w<Q, R>(p) * ev.xo[p];
+    R t[D];
+#pragma unroll
+    for (int j = 0; j < D; j++) t[j] = Mp[p][j] * df;
 #pragma unroll
     for (int i = 0; i < D; i++) {
       const int ci = Lat<Q>::c(p, i);
       if (ci == 0) continue;
 #pragma unroll
       for (int j = 0; j < D; j++) {
-        const R mm = (k.K[p][j] + k.K[p + H][j]) * df;
         if (ci > 0)
-          dP[i][j] += mm;
+          ev.dP[i][j] += t[j];
         else
-          dP[i][j] -= mm;
+          ev.dP[i][j] -= t[j];
       }
     }
   }
-  R tr = R(0);
+  ev.tr = R(0);
   const R cr = cpi * rho;
 #pragma unroll
   for (int i = 0; i < D; i++) {
 #pragma unroll
-    for (int j = 0; j < D; j++) dP[i][j] *= cr;
-    tr += dP[i][i];
+    for (int j = 0; j < D; j++) ev.dP[i][j] *= cr;
+    ev.tr += ev.dP[i][i];
   }
+}
 
+// c_p.F and c_p.dPi.c_p for the positive direction p of a pair
+template <int Q, typename R>
+__device__ __forceinline__ void pair_dots(const EvalParts<Q, R> &ev, const R (&Phi)[Lat<Q>::D], int p,
+                                          R &cF, R &cPc) {
+  constexpr int D = Lat<Q>::D;
+  cF = R(0);
+  cPc = R(0);
 #pragma unroll
-  for (int i = 0; i < D; i++) Po[i] = Pc[i];
+  for (int i = 0; i < D; i++) {
+    const int ci = Lat<Q>::c(p, i);
+    if (ci == 0) continue;
+    if (ci > 0)
+      cF += Phi[i];
+    else
+      cF -= Phi[i];
 #pragma unroll
-  for (int a = 0; a < Q; a++) {
-    // deltaN_a = w_a J [c.F/T0 + (c.dPi.c/T0 - tr dPi)/T0]   (Eq. 31), 1/T0 = 3
-    R cF = R(0), cPc = R(0);
-#pragma unroll
-    for (int i = 0; i < D; i++) {
-      const int ci = Lat<Q>::c(a, i);
-      if (ci == 0) continue;
-      if (ci > 0)
-        cF += Phi[i];
+    for (int j = 0; j < D; j++) {
+      const int cj = Lat<Q>::c(p, j);
+      if (cj == 0) continue;
+      if (ci * cj > 0)
+        cPc += ev.dP[i][j];
       else
-        cF -= Phi[i];
-#pragma unroll
-      for (int j = 0; j < D; j++) {
-        const int cj = Lat<Q>::c(a, j);
-        if (cj == 0) continue;
-        if (ci * cj > 0)
-          cPc += dP[i][j];
-        else
-          cPc -= dP[i][j];
-      }
+        cPc -= ev.dP[i][j];
     }
-    const R w = lat_w<Q, R>(a);
-    const R dN = w * (R(3) * cF + k.J * (R(3) * (R(3) * cPc - tr)));
-    // N'_a = N_a + Omega_a + deltaN_a with Omega_a = -(N_a - J f^eq_a)/tau (Eqs. 12, 20);
-    // N_a - J f^eq_a = (d_a - w_a mdev) - w_a m x_a
-    const int pa = a <= H ? a : a - H;
-    const R xa = a == 0 ? xe[0] : (a <= H ? xe[pa] + xo[pa] : xe[pa] - xo[pa]);
-    const R neq = (d[a] - w * mdev) - (w * m) * xa;
-    const R dpa = d[a] - neq * itau + dN;
-    dp[a] = dpa;
-    // J F^i gets -1/2 sum_a K^i_a d'_a   (Eq. 27; the reference part sits in Pc)
-    if (a != 0) {
+  }
+}
+
+// Phi_new = J F_new (Eq. 27 plus the body force) without forming N'. With
+//   N'_a - w_a n_ref = (1 - 1/tau) d_a + (w_a mdev + w_a m x_a)/tau + deltaN_a
+// the sum -1/2 sum_a K_a (N'_a - w_a n_ref) splits into the cell constant
+// Pb = Pc - 1/2 [(1 - 1/tau) sum_a K_a d_a + mdev sum_a w_a K_a / tau] and
+//   -1/2 [(m/tau) sum_p w_p (M_p xe_p + Dk_p xo_p) + sum_p (M_p E_p + Dk_p O_p)],
+// where deltaN_p = E_p + O_p, deltaN_pbar = E_p - O_p (Eq. 31, 1/T0 = 3):
+//   E_p = 3 w_p J (3 c_p.dPi.c_p - tr dPi),  O_p = 3 w_p c_p.Phi
+template <int Q, typename R>
+__device__ __forceinline__ void eval_phi(const CellCoef<Q, R> &k, const R (&Mp)[Lat<Q>::H + 1][Lat<Q>::D],
+                                         const R (&Dk)[Lat<Q>::H + 1][Lat<Q>::D],
+                                         const R (&U)[Lat<Q>::D], R rho, R h2m, R m,
+                                         const R (&Phi)[Lat<Q>::D], const R (&Pb)[Lat<Q>::D],
+                                         R itau, R cpi, R (&Pn)[Lat<Q>::D]) {
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  EvalParts<Q, R> ev;
+  eval_parts<Q, R>(k, Mp, U, rho, h2m, Phi, cpi, ev);
+  R acc[D];
 #pragma unroll
-      for (int i = 0; i < D; i++) Po[i] -= R(0.5) * k.K[a][i] * dpa;
-    }
+  for (int i = 0; i < D; i++) acc[i] = R(0);
+  const R mt = m * itau;
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    R cF, cPc;
+    pair_dots<Q, R>(ev, Phi, p, cF, cPc);
+    const R w = lat_w<Q, R>(p);
+    const R Ep = R(3) * w * k.J * (R(3) * cPc - ev.tr) + mt * w * ev.xe[p];
+    const R Op = R(3) * w * cF + mt * w * ev.xo[p];
+#pragma unroll
+    for (int i = 0; i < D; i++) acc[i] += Mp[p][i] * Ep + Dk[p][i] * Op;
+  }
+#pragma unroll
+  for (int i = 0; i < D; i++) Pn[i] = Pb[i] - R(0.5) * acc[i];
+}
+
+// The final evaluation: post-collision deviations dp_a = N'_a - w_a n_ref,
+//   N'_a = N_a + Omega_a + deltaN_a, Omega_a = -(N_a - J f^eq_a)/tau (Eqs. 12, 20),
+//   N_a - J f^eq_a = (d_a - w_a mdev) - w_a m x_a
+template <int Q, typename R>
+__device__ __forceinline__ void eval_np(const R (&d)[Q], const CellCoef<Q, R> &k,
+                                        const R (&Mp)[Lat<Q>::H + 1][Lat<Q>::D],
+                                        const R (&U)[Lat<Q>::D], R rho, R h2m, R m, R mdev,
+                                        const R (&Phi)[Lat<Q>::D], R itau, R cpi, R (&dp)[Q]) {
+  constexpr int H = Lat<Q>::H;
+  EvalParts<Q, R> ev;
+  eval_parts<Q, R>(k, Mp, U, rho, h2m, Phi, cpi, ev);
+  {
+    const R w = lat_w<Q, R>(0);
+    const R E0 = R(3) * w * k.J * (-ev.tr);
+    const R neq = (d[0] - w * mdev) - (w * m) * ev.xe[0];
+    dp[0] = d[0] - neq * itau + E0;
+  }
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    R cF, cPc;
+    pair_dots<Q, R>(ev, Phi, p, cF, cPc);
+    const R w = lat_w<Q, R>(p);
+    const R Ep = R(3) * w * k.J * (R(3) * cPc - ev.tr);
+    const R Op = R(3) * w * cF;
+    const R wm = w * m, wd = w * mdev;
+    const R neqp = (d[p] - wd) - wm * (ev.xe[p] + ev.xo[p]);
+    const R neqm = (d[p + H] - wd) - wm * (ev.xe[p] - ev.xo[p]);
+    dp[p] = d[p] - neqp * itau + (Ep + Op);
+    dp[p + H] = d[p + H] - neqm * itau + (Ep - Op);
   }
 }
 
@@ -154,7 +211,7 @@ template <int Q, typename R, bool CHORD, bool FINAL>
 __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, R> &k, R nref,
                                              R tau, R tol, int max_iter, R (&dp)[Q],
                                              CollideState<Q, R> &st) {
-  constexpr int D = Lat<Q>::D;
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   const R epsn = sizeof(R) == 4 ? R(64.0 / 16777216.0) : R(64.0 / 9007199254740992.0);
   R mdev = R(0);
 #pragma unroll
@@ -175,32 +232,45 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
     }
     st.U[i] = s * im;
   }
+  // pair sums and differences of the link coefficients
+  R Mp[H + 1][D], Dk[H + 1][D];
+#pragma unroll
+  for (int i = 0; i < D; i++) Mp[0][i] = Dk[0][i] = R(0);
+#pragma unroll
+  for (int p = 1; p <= H; p++)
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      Mp[p][i] = k.K[p][i] + k.K[p + H][i];
+      Dk[p][i] = k.K[p][i] - k.K[p + H][i];
+    }
+  const R itau = R(1) / tau;
+  const R cpi = -R(0.5) * (R(1) - R(0.5) * itau);
   // constant part of J F: body force m G, 1/2 sum_a L_a N_a (L_a = -K_abar) and the
   // reference part -n_ref sum_a w_a K_a of both sums of Eq. 27. The last is the
   // largest term and is the same every step, so it is formed without rounding
-  // error from the split coefficient KW + KWL.
-  R Pc[D];
+  // error from the split coefficient KW + KWL. Pb adds the parts of
+  // -1/2 sum_a K_a N'_a that do not change during the iteration.
+  R Pb[D];
 #pragma unroll
   for (int i = 0; i < D; i++) {
-    const R p = nref * k.Kw[i];
-    const R err = two_prod_err(nref, k.Kw[i], p) + nref * k.KwL[i];
-    Pc[i] = m * k.G[i] - err;
+    const R pr = nref * k.Kw[i];
+    const R err = two_prod_err(nref, k.Kw[i], pr) + nref * k.KwL[i];
+    R s = m * k.G[i] - err - R(0.5) * itau * mdev * k.Kw[i];
+    R sd = R(0);
+#pragma unroll
+    for (int a = 1; a < Q; a++) {
+      s -= R(0.5) * k.K[lat_opp<Q>(a)][i] * d[a];
+      sd += k.K[a][i] * d[a];
+    }
+    Pb[i] = (s - R(0.5) * (R(1) - itau) * sd) - pr;
   }
-#pragma unroll
-  for (int a = 1; a < Q; a++)
-#pragma unroll
-    for (int i = 0; i < D; i++) Pc[i] -= R(0.5) * k.K[lat_opp<Q>(a)][i] * d[a];
-#pragma unroll
-  for (int i = 0; i < D; i++) Pc[i] -= nref * k.Kw[i];
-  const R itau = R(1) / tau;
-  const R cpi = -R(0.5) * (R(1) - R(0.5) * itau);
   R Phi[D], Pn[D];
 #pragma unroll
   for (int i = 0; i < D; i++) Phi[i] = CHORD ? m * k.Fr[i] : R(0);
   st.conv = false;
   int it = 0;
   while (it < max_iter) {
-    collide_eval<Q, R>(d, k, st.U, st.rho, h2m, m, mdev, Phi, Pc, itau, cpi, dp, Pn);
+    eval_phi<Q, R>(k, Mp, Dk, st.U, st.rho, h2m, m, Phi, Pb, itau, cpi, Pn);
     it++;
     R r[D];
 #pragma unroll
@@ -227,7 +297,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
   const R iJ = R(1) / k.J;
 #pragma unroll
   for (int i = 0; i < D; i++) st.F[i] = Phi[i] * iJ;
-  if (FINAL) collide_eval<Q, R>(d, k, st.U, st.rho, h2m, m, mdev, Phi, Pc, itau, cpi, dp, Pn);
+  if (FINAL) eval_np<Q, R>(d, k, Mp, st.U, st.rho, h2m, m, mdev, Phi, itau, cpi, dp);
 }
 
 }  // namespace vlb

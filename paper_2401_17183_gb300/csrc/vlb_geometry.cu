@@ -422,13 +422,17 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
       double s = 0.0;
       for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
       k.G[i] = s;
-      k.Kw[i] = 0.0;
       k.KwL[i] = 0.0;
       k.Fr[i] = 0.0;
       for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
     }
     for (int av = 0; av < Q; av++)
       for (int i = 0; i < D; i++) k.K[av][i] = a.K[(c * Q + av) * D + i];
+    for (int i = 0; i < D; i++) {
+      double s = 0.0;
+      for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * k.K[av][i];
+      k.Kw[i] = s;  // sum_a w_a K_a
+    }
     double Hm[D][D];
     chord_matrix<Q>(k, a.tau, Hm);
     for (int i = 0; i < D; i++)
