@@ -13,26 +13,40 @@ struct Grid {
   int32_t wall[3];
 };
 
-template <int Q>
+template <int Q, typename IT = int64_t>
 struct Addr {
   static constexpr int D = Lat<Q>::D;
-  int64_t cell;
-  int64_t ic[3];
-  int64_t dp[3], dm[3];
+  IT cell;
+  IT ic[3];
+  IT dp[3], dm[3];
   bool lo[3], hi[3];
 
-  __device__ __forceinline__ Addr(const Grid &g, int64_t c) : cell(c) {
+  // from a linear cell index (divisions; used outside the hot kernel)
+  __device__ __forceinline__ Addr(const Grid &g, int64_t c) {
     int64_t r = c;
-    ic[2] = r % g.n[2];
+    ic[2] = (IT)(r % g.n[2]);
     r /= g.n[2];
-    ic[1] = r % g.n[1];
-    ic[0] = r / g.n[1];
+    ic[1] = (IT)(r % g.n[1]);
+    ic[0] = (IT)(r / g.n[1]);
+    cell = (IT)c;
+    init(g);
+  }
+  // from index coordinates
+  __device__ __forceinline__ Addr(const Grid &g, IT i0, IT i1, IT i2) {
+    ic[0] = i0;
+    ic[1] = i1;
+    ic[2] = i2;
+    cell = (i0 * (IT)g.n[1] + i1) * (IT)g.n[2] + i2;
+    init(g);
+  }
+  __device__ __forceinline__ void init(const Grid &g) {
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-      dp[d] = (ic[d] == g.n[d] - 1) ? -(g.n[d] - 1) * g.s[d] : g.s[d];
-      dm[d] = (ic[d] == 0) ? (g.n[d] - 1) * g.s[d] : -g.s[d];
+      const IT n = (IT)g.n[d], st = (IT)g.s[d];
+      dp[d] = (ic[d] == n - 1) ? -(n - 1) * st : st;
+      dm[d] = (ic[d] == 0) ? (n - 1) * st : -st;
       lo[d] = g.wall[d] && ic[d] == 0;
-      hi[d] = g.wall[d] && ic[d] == g.n[d] - 1;
+      hi[d] = g.wall[d] && ic[d] == n - 1;
     }
   }
   __device__ __forceinline__ bool wall_cell() const {
@@ -54,8 +68,8 @@ struct Addr {
     return x;
   }
   // linear index of q + sg c_a (periodic wrap on every axis)
-  __device__ __forceinline__ int64_t nb(int a, int sg) const {
-    int64_t r = cell;
+  __device__ __forceinline__ IT nb(int a, int sg) const {
+    IT r = cell;
 #pragma unroll
     for (int d = 0; d < D; d++) {
       const int cd = sg * Lat<Q>::c(a, d);
@@ -69,8 +83,9 @@ struct Addr {
 // Arrived populations N_a(q, t). Even parity: slot a of q. Odd parity (the
 // layout an even step leaves behind): slot abar of q - c_a, or slot a of q
 // when q - c_a lies beyond a wall (halfway bounce-back).
-template <int Q, bool ODD, typename S, typename R>
-__device__ __forceinline__ void pull(const S *f, int64_t ps, const Addr<Q> &ad, R (&N)[Q]) {
+template <int Q, bool ODD, typename S, typename R, typename IT>
+__device__ __forceinline__ void pull(const S *__restrict__ f, IT ps, const Addr<Q, IT> &ad,
+                                     R (&N)[Q]) {
 #pragma unroll
   for (int a = 0; a < Q; a++) {
     if (!ODD || a == 0) {

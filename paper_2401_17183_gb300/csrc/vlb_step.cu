@@ -25,55 +25,67 @@ struct StepArgs {
   Grid g;
   int64_t ncell;
   int64_t cstride;  // records in the coefficient array
-  int64_t nfast;    // plane mode: record = cell / nfast
+  int32_t plane;    // one coefficient record per column of the fastest axis
   double tau, tol;
   double nref;      // populations are stored as N_a - w_a nref
   int32_t max_iter;
   int32_t moving;
 };
 
-template <int Q, typename S, typename R, bool ODD, bool PLANE>
-__global__ void __launch_bounds__(128) k_step(const StepArgs a) {
+// One thread per cell. The grid is (tiles of the fastest axis, the middle
+// axis, the slowest axis), so a thread finds its cell without a division and
+// the 32 cells of a warp share every other coordinate: wall tests are
+// warp-uniform and, in plane mode, so is the coefficient record. IT is the
+// index type: 32-bit whenever q * ncell fits.
+constexpr int kStepThreads = 128;
+
+template <int Q, typename S, typename R, bool ODD, typename IT>
+__global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? 3 : 1) k_step(const StepArgs a) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
-  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= a.ncell) return;
-  S *f = static_cast<S *>(a.f);
-  const R *coef = static_cast<const R *>(a.coef);
-  const int64_t ps = a.ncell;
-  const Addr<Q> ad(a.g, cell);
+  const IT ifast = (IT)blockIdx.x * kStepThreads + (IT)threadIdx.x;
+  const IT nfast = (IT)(D == 3 ? a.g.n[2] : a.g.n[1]);
+  if (ifast >= nfast) return;
+  const Addr<Q, IT> ad = D == 3 ? Addr<Q, IT>(a.g, (IT)blockIdx.z, (IT)blockIdx.y, ifast)
+                                : Addr<Q, IT>(a.g, (IT)blockIdx.y, ifast, (IT)0);
+  const IT cell = ad.cell;
+  S *__restrict__ f = static_cast<S *>(a.f);
+  const R *__restrict__ coef = static_cast<const R *>(a.coef);
+  const IT ps = (IT)a.ncell;
 
   // ---- pull (read side of Eq. 22): deviations d_a = N_a - w_a n_ref
   R N[Q];
-  pull<Q, ODD, S, R>(f, ps, ad, N);
+  pull<Q, ODD, S, R, IT>(f, ps, ad, N);
 
-  // ---- coefficients
-  const int64_t rec = PLANE ? cell / a.nfast : cell;
-  const int64_t cs = a.cstride;
+  // ---- coefficients: one record per column of the fastest axis (plane mode)
+  // or per cell
+  const IT rec = a.plane ? (D == 3 ? (IT)blockIdx.z * (IT)a.g.n[1] + (IT)blockIdx.y : (IT)blockIdx.y)
+                         : cell;
+  const IT cs = (IT)a.cstride;
+  const R *__restrict__ cr = coef + rec;
   CellCoef<Q, R> k;
-  k.J = coef[L::J * cs + rec];
+  k.J = __ldg(cr + L::J * cs);
 #pragma unroll
-  for (int i = 0; i < L::NS; i++) k.gd[i] = coef[(L::GINV + i) * cs + rec];
+  for (int i = 0; i < L::NS; i++) k.gd[i] = __ldg(cr + (L::GINV + i) * cs);
 #pragma unroll
   for (int i = 0; i < D; i++) {
-    k.G[i] = coef[(L::BODY + i) * cs + rec];
-    k.Kw[i] = coef[(L::KW + i) * cs + rec];
-    k.KwL[i] = coef[(L::KWL + i) * cs + rec];
-    k.Fr[i] = coef[(L::FR + i) * cs + rec];
+    k.G[i] = __ldg(cr + (L::BODY + i) * cs);
+    k.Kw[i] = __ldg(cr + (L::KW + i) * cs);
+    k.KwL[i] = __ldg(cr + (L::KWL + i) * cs);
+    k.Fr[i] = __ldg(cr + (L::FR + i) * cs);
     k.K[0][i] = R(0);
 #pragma unroll
-    for (int j = 0; j < D; j++) k.Hm[i][j] = coef[(L::HM + i * D + j) * cs + rec];
+    for (int j = 0; j < D; j++) k.Hm[i][j] = __ldg(cr + (L::HM + i * D + j) * cs);
   }
 #pragma unroll
   for (int av = 1; av < Q; av++)
 #pragma unroll
-    for (int i = 0; i < D; i++) k.K[av][i] = coef[(L::K + (av - 1) * D + i) * cs + rec];
+    for (int i = 0; i < D; i++) k.K[av][i] = __ldg(cr + (L::K + (av - 1) * D + i) * cs);
 
   // ---- collide (section 2.2)
   R Np[Q];
   CollideState<Q, R> cst;
-  collide_cell<Q, R, true, true>(N, k, R(a.nref), R(a.tau), R(a.tol), a.max_iter, Np,
-                                           cst);
+  collide_cell<Q, R, true, true>(N, k, R(a.nref), R(a.tau), R(a.tol), a.max_iter, Np, cst);
   if (!cst.conv) atomicOr(a.err, ERR_NOCONV);
 
   // ---- moving walls: a reflected population is corrected by
@@ -81,7 +93,7 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs a) {
   const bool moving = a.moving && ad.wall_cell();
   R uw[D];
 #pragma unroll
-  for (int i = 0; i < D; i++) uw[i] = moving ? coef[(L::UW + i) * cs + rec] : R(0);
+  for (int i = 0; i < D; i++) uw[i] = moving ? __ldg(cr + (L::UW + i) * cs) : R(0);
   EqParts<Q, R> ew;
   if (moving) {
     R zero[D];
@@ -94,15 +106,15 @@ __global__ void __launch_bounds__(128) k_step(const StepArgs a) {
 #pragma unroll
   for (int av = 1; av < Q; av++) {
     const int ab = lat_opp<Q>(av);
-    const bool cr = ad.crosses(av, 1);
+    const bool crs = ad.crosses(av, 1);
     R v = Np[av];
-    if (moving && cr) {
+    if (moving && crs) {
       const int p = av <= H ? av : av - H;
       const R O = eq_odd<Q, R>(ew, uw, p);
       const R corr = R(2) * k.J * cst.rho * lat_w<Q, R>(av) * O;
       v -= (av <= H) ? corr : -corr;
     }
-    if (!ODD || cr)
+    if (!ODD || crs)
       f[ab * ps + cell] = static_cast<S>(v);
     else
       f[av * ps + ad.nb(av, 1)] = static_cast<S>(v);
@@ -120,7 +132,7 @@ static cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
   a.g = make_grid(m);
   a.ncell = m->ncell;
   a.cstride = sim->ncoef;
-  a.nfast = m->md.n[m->md.dim - 1];
+  a.plane = sim->plane;
   a.tau = sim->p.tau;
   a.tol = sim->p.tol;
   a.nref = sim->nref;
@@ -130,18 +142,22 @@ static cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
     for (int sd = 0; sd < 2; sd++)
       for (int d = 0; d < 3; d++)
         if (sim->p.wall_u[ax][sd][d] != 0.0 || sim->p.wall_omega[ax][sd][d] != 0.0) a.moving = 1;
-  const int threads = 128;
-  const int64_t blocks = (m->ncell + threads - 1) / threads;
-  if (sim->plane) {
+  const int dim = m->md.dim;
+  const int64_t nfast = dim == 3 ? m->md.n[2] : m->md.n[1];
+  dim3 grid((unsigned)((nfast + kStepThreads - 1) / kStepThreads),
+            (unsigned)(dim == 3 ? m->md.n[1] : m->md.n[0]), (unsigned)(dim == 3 ? m->md.n[0] : 1));
+  // 32-bit indexing when every population offset fits
+  const bool i32 = (int64_t)Q * m->ncell < ((int64_t)1 << 31) && sim->ncoef * (int64_t)sim->nc < ((int64_t)1 << 31);
+  if (i32) {
     if (odd)
-      k_step<Q, S, R, true, true><<<(unsigned)blocks, threads, 0, s>>>(a);
+      k_step<Q, S, R, true, int32_t><<<grid, kStepThreads, 0, s>>>(a);
     else
-      k_step<Q, S, R, false, true><<<(unsigned)blocks, threads, 0, s>>>(a);
+      k_step<Q, S, R, false, int32_t><<<grid, kStepThreads, 0, s>>>(a);
   } else {
     if (odd)
-      k_step<Q, S, R, true, false><<<(unsigned)blocks, threads, 0, s>>>(a);
+      k_step<Q, S, R, true, int64_t><<<grid, kStepThreads, 0, s>>>(a);
     else
-      k_step<Q, S, R, false, false><<<(unsigned)blocks, threads, 0, s>>>(a);
+      k_step<Q, S, R, false, int64_t><<<grid, kStepThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
