@@ -159,15 +159,22 @@ __device__ __forceinline__ void eval_phi(const CellCoef<Q, R> &k, const R (&Mp)[
 
 // The final evaluation: post-collision deviations dp_a = N'_a - w_a n_ref,
 //   N'_a = N_a + Omega_a + deltaN_a, Omega_a = -(N_a - J f^eq_a)/tau (Eqs. 12, 20),
-//   N_a - J f^eq_a = (d_a - w_a mdev) - w_a m x_a
+//   N_a - J f^eq_a = (d_a - w_a mdev) - w_a m x_a,
+// together with Phi_new at the same Phi (as eval_phi computes it).
 template <int Q, typename R>
 __device__ __forceinline__ void eval_np(const R (&d)[Q], const CellCoef<Q, R> &k,
                                         const R (&Mp)[Lat<Q>::H + 1][Lat<Q>::D],
+                                        const R (&Dk)[Lat<Q>::H + 1][Lat<Q>::D],
                                         const R (&U)[Lat<Q>::D], R rho, R h2m, R m, R mdev,
-                                        const R (&Phi)[Lat<Q>::D], R itau, R cpi, R (&dp)[Q]) {
-  constexpr int H = Lat<Q>::H;
+                                        const R (&Phi)[Lat<Q>::D], const R (&Pb)[Lat<Q>::D],
+                                        R itau, R cpi, R (&dp)[Q], R (&Pn)[Lat<Q>::D]) {
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   EvalParts<Q, R> ev;
   eval_parts<Q, R>(k, Mp, U, rho, h2m, Phi, cpi, ev);
+  R acc[D];
+#pragma unroll
+  for (int i = 0; i < D; i++) acc[i] = R(0);
+  const R mt = m * itau;
   {
     const R w = lat_w<Q, R>(0);
     const R E0 = R(3) * w * k.J * (-ev.tr);
@@ -186,6 +193,66 @@ __device__ __forceinline__ void eval_np(const R (&d)[Q], const CellCoef<Q, R> &k
     const R neqm = (d[p + H] - wd) - wm * (ev.xe[p] - ev.xo[p]);
     dp[p] = d[p] - neqp * itau + (Ep + Op);
     dp[p + H] = d[p + H] - neqm * itau + (Ep - Op);
+    const R Ea = Ep + mt * w * ev.xe[p];
+    const R Oa = Op + mt * w * ev.xo[p];
+#pragma unroll
+    for (int i = 0; i < D; i++) acc[i] += Mp[p][i] * Ea + Dk[p][i] * Oa;
+  }
+#pragma unroll
+  for (int i = 0; i < D; i++) Pn[i] = Pb[i] - R(0.5) * acc[i];
+}
+
+// First-order move of dp from Phi to Phi + dPhi. With U~ = U + Phi/(2m):
+//   d dp_a / dPhi . dPhi = (w_a / (2 tau)) dx_a/dU~ . dPhi + 3 w_a c_a . dPhi
+// where dx_a/dU~ takes the U~ U~ terms of B (even in c_a) and the g^ij U~
+// terms of C (odd in c_a):
+//   even: 9 (c.U~)(c.dPhi) - 3 U~.dPhi
+//   odd : 9/2 [(c.g.c)(c.dPhi) - T0 (2 c.g.dPhi + tr(g) c.dPhi)]
+// The terms left out (the cubic U~ U~ U~ part and deltaPi) are of order |U|^2
+// and Theta^2 relative to these, so for the small last correction of the
+// chord iteration this leaves an error far below the FP32 unit roundoff.
+template <int Q, typename R>
+__device__ __forceinline__ void extrapolate(const CellCoef<Q, R> &k, const R (&U)[Lat<Q>::D],
+                                            const R (&Phi)[Lat<Q>::D], R h2m,
+                                            const R (&dPhi)[Lat<Q>::D], R itau, R (&dp)[Q]) {
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  R Ut[D], gD[D], trg = R(D), UD = R(0);
+#pragma unroll
+  for (int i = 0; i < D; i++) Ut[i] = U[i] + Phi[i] * h2m;
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    R s = dPhi[i];
+#pragma unroll
+    for (int j = 0; j < D; j++) s += k.gd[sym<D>(i, j)] * dPhi[j];
+    gD[i] = s;  // g . dPhi
+    trg += k.gd[sym<D>(i, i)];
+    UD += Ut[i] * dPhi[i];
+  }
+  const R ht = R(0.5) * itau;
+  dp[0] += ht * lat_w<Q, R>(0) * (-R(3) * UD);
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    R cD = R(0), cU = R(0), cgD = R(0), cgc = R(0);
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const int ci = Lat<Q>::c(p, i);
+      if (ci == 0) continue;
+      cD += ci > 0 ? dPhi[i] : -dPhi[i];
+      cU += ci > 0 ? Ut[i] : -Ut[i];
+      cgD += ci > 0 ? gD[i] : -gD[i];
+      cgc += R(1);
+#pragma unroll
+      for (int j = 0; j < D; j++) {
+        const int cj = Lat<Q>::c(p, j);
+        if (cj == 0) continue;
+        cgc += ci * cj > 0 ? k.gd[sym<D>(i, j)] : -k.gd[sym<D>(i, j)];
+      }
+    }
+    const R w = lat_w<Q, R>(p);
+    const R ev = ht * w * (R(9) * cU * cD - R(3) * UD);
+    const R od = ht * w * R(4.5) * (cgc * cD - R(kT0) * (R(2) * cgD + trg * cD)) + R(3) * w * cD;
+    dp[p] += ev + od;
+    dp[p + H] += ev - od;
   }
 }
 
@@ -197,16 +264,18 @@ __device__ __forceinline__ double two_prod_err(double x, double y, double p) { r
 //   Phi <- Phi + H (J G - Phi),  H = (I - L)^-1,
 // where L is the part of dG/dF that depends only on the cell geometry (it
 // comes from the g^ij U~ terms of Eq. 33 and the c.F term of Eq. 31; the
-// remainder is of order |U| Theta). With CHORD = false, H = I (plain
-// fixed-point iteration) and the start value is Phi = 0; with CHORD, the start
-// value is m times the rest-state force. The iteration stops when the
-// correction is at most max(tol max(m, |Phi|), 64 eps |Phi|): eps is the unit
-// roundoff of R, and Phi is a sum of some forty rounded terms of its own size,
-// so corrections below a few tens of ulp are rounding noise. N' is then
-// evaluated once more with the corrected Phi; the chord step leaves that Phi
-// about |L| |U| times the last correction away from the fixed point, which is
-// what makes N' accurate to the precision of the arithmetic. (FINAL = false
-// skips that evaluation when only F is wanted.)
+// remainder is of order |U| Theta, so each chord step shrinks the error by
+// about that factor). With CHORD = false, H = I (plain fixed-point iteration)
+// and the start value is Phi = 0; with CHORD, the start value is m times the
+// rest-state force. A correction is accepted as converged when it is at most
+// max(tol max(m, |Phi|), 64 eps |Phi|): eps is the unit roundoff of R, and
+// Phi is a sum of some forty rounded terms of its own size, so smaller
+// corrections are rounding noise.
+// With FINAL every evaluation also forms N'. When the correction of an
+// evaluation is accepted, N' is moved by that correction to first order
+// (extrapolate), so the returned N' belongs to the corrected Phi and no
+// further evaluation is needed: a cell whose start value is already within
+// the tolerance costs a single evaluation.
 template <int Q, typename R, bool CHORD, bool FINAL>
 __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, R> &k, R nref,
                                              R tau, R tol, int max_iter, R (&dp)[Q],
@@ -269,35 +338,64 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
   for (int i = 0; i < D; i++) Phi[i] = CHORD ? m * k.Fr[i] : R(0);
   st.conv = false;
   int it = 0;
-  while (it < max_iter) {
-    eval_phi<Q, R>(k, Mp, Dk, st.U, st.rho, h2m, m, Phi, Pb, itau, cpi, Pn);
-    it++;
+  // correction dF = H (Phi_new - Phi); converged when it is at most
+  // max(tol max(m, |Phi|), 64 eps |Phi|)
+  auto correction = [&](R(&dF)[D]) -> bool {
     R r[D];
 #pragma unroll
     for (int i = 0; i < D; i++) r[i] = Pn[i] - Phi[i];
     R diff = R(0), pmax = R(0);
 #pragma unroll
     for (int i = 0; i < D; i++) {
-      R dF = r[i];
+      R x = r[i];
       if (CHORD) {
-        dF = R(0);
+        x = R(0);
 #pragma unroll
-        for (int j = 0; j < D; j++) dF += k.Hm[i][j] * r[j];
+        for (int j = 0; j < D; j++) x += k.Hm[i][j] * r[j];
       }
-      diff = maxnan(diff, absr(dF));
+      dF[i] = x;
+      diff = maxnan(diff, absr(x));
       pmax = maxnan(pmax, absr(Phi[i]));
-      Phi[i] += dF;
     }
-    if (diff <= maxnan(tol * maxnan(m, pmax), epsn * pmax)) {
-      st.conv = true;
-      break;
+    return diff <= maxnan(tol * maxnan(m, pmax), epsn * pmax);
+  };
+  if (!FINAL) {
+    // F only: plain iteration on Phi_new
+    while (it < max_iter) {
+      eval_phi<Q, R>(k, Mp, Dk, st.U, st.rho, h2m, m, Phi, Pb, itau, cpi, Pn);
+      it++;
+      R dF[D];
+      const bool ok = correction(dF);
+#pragma unroll
+      for (int i = 0; i < D; i++) Phi[i] += dF[i];
+      if (ok) {
+        st.conv = true;
+        break;
+      }
+    }
+  } else {
+    // every evaluation also forms N'; the accepted correction is applied to
+    // N' by extrapolation
+    while (it < max_iter) {
+      eval_np<Q, R>(d, k, Mp, Dk, st.U, st.rho, h2m, m, mdev, Phi, Pb, itau, cpi, dp, Pn);
+      it++;
+      R dF[D];
+      const bool ok = correction(dF);
+      if (ok) {
+        extrapolate<Q, R>(k, st.U, Phi, h2m, dF, itau, dp);
+#pragma unroll
+        for (int i = 0; i < D; i++) Phi[i] += dF[i];
+        st.conv = true;
+        break;
+      }
+#pragma unroll
+      for (int i = 0; i < D; i++) Phi[i] += dF[i];
     }
   }
   st.iters = it;
   const R iJ = R(1) / k.J;
 #pragma unroll
   for (int i = 0; i < D; i++) st.F[i] = Phi[i] * iJ;
-  if (FINAL) eval_np<Q, R>(d, k, Mp, st.U, st.rho, h2m, m, mdev, Phi, itau, cpi, dp);
 }
 
 }  // namespace vlb
