@@ -134,6 +134,24 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x, device=None):
+    """Max of a per-rank float over all ranks of the default process group
+    (returned unchanged when no group is initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, ncell, steps, seconds):
+    """Whole-job cell updates per second (millions): every rank advances its own
+    replica of ncell cells by steps steps; seconds is the slowest rank's time."""
+    return world * ncell * steps / seconds / 1e6
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -277,11 +295,8 @@ def main():
     clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
     sim.sync()     # raises on a kernel-reported error (e.g. a non-converged solve)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ncell * a.steps / (ms / 1e3) / 1e6
+    ms = max_over_ranks(ms, dev)
+    value = job_mlups(world, ncell, a.steps, ms / 1e3)
     per_launch_s = ms / 1e3 / a.steps
     bpc = BYTES_PER_CELL[("19", "f32")]
     peak, peak_kind = measured_peak_hbm()
@@ -304,14 +319,10 @@ def main():
         sim.reset_ptr(pin_rho.data_ptr(), pin_u.data_ptr())
         sim.step(a.steps)
         sim.moments_ptr(out_rho.data_ptr(), out_u.data_ptr(), out_ut.data_ptr(), out_t.data_ptr())
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, dev)
         h2d = 8 * ncell * 4
         d2h = 8 * ncell * 7 + 56
-        e2e = {"value": world * ncell * a.steps / el / 1e6, "unit": "MLUPS",
+        e2e = {"value": job_mlups(world, ncell, a.steps, el), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
                "api": "vlb_reset(host rho,u) + vlb_step(K) + vlb_moments(host rho,u,u~,totals)"}
 
