@@ -283,8 +283,10 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
   }
   s->plane = plane ? 1 : 0;
   s->ncoef = plane ? mesh->ncell / mesh->md.n[dim - 1] : mesh->ncell;
-  s->nc = q == 9 ? vlb::CoefLayout<9>::NC : vlb::CoefLayout<19>::NC;
-  const size_t es = params->precision == VLB_F64 ? 8 : 4;
+  const bool f64 = params->precision == VLB_F64;
+  s->nc = q == 9 ? (f64 ? vlb::CoefLayout<9>::stride<double>() : vlb::CoefLayout<9>::stride<float>())
+                 : (f64 ? vlb::CoefLayout<19>::stride<double>() : vlb::CoefLayout<19>::stride<float>());
+  const size_t es = f64 ? 8 : 4;
   cudaError_t e = cudaMalloc(&s->d_f, es * q * mesh->ncell);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_coef, es * s->nc * s->ncoef);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));

@@ -9,7 +9,13 @@
 // The reference is the same in every cell, so advection and bounce-back move
 // deviations exactly as they move populations, while every product below
 // works on small numbers: that keeps FP32 rounding relative to the deviation,
-// not to N.
+// not to N. The force is carried as Phi = J F, which keeps J out of every
+// product formed once per step with the same operands.
+//
+// Directions come in pairs (p, pbar = p + H) with c_pbar = -c_p; every sum over
+// directions below is a sum over pairs of an even part (same for p and pbar)
+// and an odd part (opposite signs), with the link coefficients stored as
+// M_p = K_p + K_pbar and D_p = K_p - K_pbar.
 #pragma once
 
 #include "vlb_internal.cuh"
@@ -26,14 +32,10 @@ struct CollideState {
   bool conv;
 };
 
-// Direction-independent part of one collision evaluation for a given
-// Phi = J F: the equilibrium of Eq. 33 as J f^eq_a = w_a m (1 + x_a) with
-// x_p = xe_p + xo_p and x_pbar = xe_p - xo_p (only x is formed, never 1 + x),
-// and the symmetric part of deltaPi (Eq. 30) as dS[i][j] = dPi^ij + dPi^ji
-// halved, with its trace.
-//   m = sum N = n_ref + mdev,  rho = m / J,  U~ = U + Phi / (2 m)
-// Working with J F rather than F keeps J out of every product that is formed
-// once per step with the same operands.
+// Direction-independent part of one evaluation for a given Phi: the
+// equilibrium of Eq. 33 as J f^eq_a = w_a m (1 + x_a), x_p = xe_p + xo_p,
+// x_pbar = xe_p - xo_p (only x is formed, never 1 + x), and deltaPi of Eq. 30
+// with its trace.
 template <int Q, typename R>
 struct EvalParts {
   static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
@@ -42,15 +44,32 @@ struct EvalParts {
   R tr;
 };
 
+// weight class of a direction: 0 rest, 1 axis, 2 diagonal
+template <int Q>
+__host__ __device__ constexpr int wclass(int a) {
+  return a == 0 ? 0 : lat_nnz<Q>(a) == 1 ? 1 : 2;
+}
+
+// Per-cell constants of one collision.
 template <int Q, typename R>
-__device__ __forceinline__ void eval_parts(const CellCoef<Q, R> &k, const R (&Mp)[Lat<Q>::H + 1][Lat<Q>::D],
-                                           const R (&U)[Lat<Q>::D], R rho, R h2m,
-                                           const R (&Phi)[Lat<Q>::D], R cpi,
+struct CollideConst {
+  R m, mdev, h2m, itau;
+  R dfw[3];   // -(1 - 1/(2 tau)) rho w, per weight class
+  R w9J[3];   // 9 w J
+  R w3J[3];   // 3 w J
+  R iwm[3];   // w m / tau
+  R wm[3];    // w m
+  R wd[3];    // w mdev
+};
+
+template <int Q, typename R>
+__device__ __forceinline__ void eval_parts(const CellCoef<Q, R> &k, const CollideConst<Q, R> &cc,
+                                           const R (&U)[Lat<Q>::D], const R (&Phi)[Lat<Q>::D],
                                            EvalParts<Q, R> &ev) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   R dU[D];
 #pragma unroll
-  for (int i = 0; i < D; i++) dU[i] = Phi[i] * h2m;
+  for (int i = 0; i < D; i++) dU[i] = Phi[i] * cc.h2m;
   EqParts<Q, R> e;
   eq_parts<Q, R>(k.gd, U, dU, e);
   ev.xe[0] = eq_even_dev<Q, R>(e, 0);
@@ -60,8 +79,8 @@ __device__ __forceinline__ void eval_parts(const CellCoef<Q, R> &k, const R (&Mp
     ev.xe[p] = eq_even_dev<Q, R>(e, p);
     ev.xo[p] = eq_odd<Q, R>(e, U, p);
   }
-  // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a - L^j_a) f^eq_a   (Eq. 30)
-  // with K_a - L_a = K_a + K_abar = M_p; a pair contributes c_p (f_p - f_pbar),
+  // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a - L^j_a) f^eq_a   (Eq. 30):
+  // K_a - L_a = K_a + K_abar = M_p, a pair contributes c_p (f_p - f_pbar) with
   // f_p - f_pbar = 2 rho w_p xo_p
 #pragma unroll
   for (int i = 0; i < D; i++)
@@ -69,10 +88,10 @@ __device__ __forceinline__ void eval_parts(const CellCoef<Q, R> &k, const R (&Mp
     for (int j = 0; j < D; j++) ev.dP[i][j] = R(0);
 #pragma unroll
   for (int p = 1; p <= H; p++) {
-    const R df = R(2) * lat_w<Q, R>(p) * ev.xo[p];
+    const R df = cc.dfw[wclass<Q>(p)] * ev.xo[p];
     R t[D];
 #pragma unroll
-    for (int j = 0; j < D; j++) t[j] = Mp[p][j] * df;
+    for (int j = 0; j < D; j++) t[j] = k.M[p][j] * df;
 #pragma unroll
     for (int i = 0; i < D; i++) {
       const int ci = Lat<Q>::c(p, i);
@@ -87,16 +106,11 @@ __device__ __forceinline__ void eval_parts(const CellCoef<Q, R> &k, const R (&Mp
     }
   }
   ev.tr = R(0);
-  const R cr = cpi * rho;
 #pragma unroll
-  for (int i = 0; i < D; i++) {
-#pragma unroll
-    for (int j = 0; j < D; j++) ev.dP[i][j] *= cr;
-    ev.tr += ev.dP[i][i];
-  }
+  for (int i = 0; i < D; i++) ev.tr += ev.dP[i][i];
 }
 
-// c_p.F and c_p.dPi.c_p for the positive direction p of a pair
+// c_p.Phi and c_p.dPi.c_p for the positive direction p of a pair
 template <int Q, typename R>
 __device__ __forceinline__ void pair_dots(const EvalParts<Q, R> &ev, const R (&Phi)[Lat<Q>::D], int p,
                                           R &cF, R &cPc) {
@@ -123,80 +137,73 @@ __device__ __forceinline__ void pair_dots(const EvalParts<Q, R> &ev, const R (&P
   }
 }
 
-// Phi_new = J F_new (Eq. 27 plus the body force) without forming N'. With
+// Phi_new = J F_new (Eq. 27 plus the body force) for a given Phi without
+// forming N'. With
 //   N'_a - w_a n_ref = (1 - 1/tau) d_a + (w_a mdev + w_a m x_a)/tau + deltaN_a
-// the sum -1/2 sum_a K_a (N'_a - w_a n_ref) splits into the cell constant
-// Pb = Pc - 1/2 [(1 - 1/tau) sum_a K_a d_a + mdev sum_a w_a K_a / tau] and
-//   -1/2 [(m/tau) sum_p w_p (M_p xe_p + Dk_p xo_p) + sum_p (M_p E_p + Dk_p O_p)],
-// where deltaN_p = E_p + O_p, deltaN_pbar = E_p - O_p (Eq. 31, 1/T0 = 3):
-//   E_p = 3 w_p J (3 c_p.dPi.c_p - tr dPi),  O_p = 3 w_p c_p.Phi
+// and deltaN_p = E_p + O_p, deltaN_pbar = E_p - O_p (Eq. 31, 1/T0 = 3),
+//   E_p = 3 w_p J (3 c_p.dPi.c_p - tr dPi),  O_p = 3 w_p c_p.Phi,
+// the sum -1/2 sum_a K_a (N'_a - w_a n_ref) is the cell constant Pb plus
+//   -1/2 sum_p [M_p (E_p + w_p m xe_p / tau) + D_p (O_p + w_p m xo_p / tau)].
 template <int Q, typename R>
-__device__ __forceinline__ void eval_phi(const CellCoef<Q, R> &k, const R (&Mp)[Lat<Q>::H + 1][Lat<Q>::D],
-                                         const R (&Dk)[Lat<Q>::H + 1][Lat<Q>::D],
-                                         const R (&U)[Lat<Q>::D], R rho, R h2m, R m,
-                                         const R (&Phi)[Lat<Q>::D], const R (&Pb)[Lat<Q>::D],
-                                         R itau, R cpi, R (&Pn)[Lat<Q>::D]) {
+__device__ __forceinline__ void eval_phi(const CellCoef<Q, R> &k, const CollideConst<Q, R> &cc,
+                                         const R (&U)[Lat<Q>::D], const R (&Phi)[Lat<Q>::D],
+                                         const R (&Pb)[Lat<Q>::D], R (&Pn)[Lat<Q>::D]) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   EvalParts<Q, R> ev;
-  eval_parts<Q, R>(k, Mp, U, rho, h2m, Phi, cpi, ev);
+  eval_parts<Q, R>(k, cc, U, Phi, ev);
   R acc[D];
 #pragma unroll
   for (int i = 0; i < D; i++) acc[i] = R(0);
-  const R mt = m * itau;
 #pragma unroll
   for (int p = 1; p <= H; p++) {
     R cF, cPc;
     pair_dots<Q, R>(ev, Phi, p, cF, cPc);
-    const R w = lat_w<Q, R>(p);
-    const R Ep = R(3) * w * k.J * (R(3) * cPc - ev.tr) + mt * w * ev.xe[p];
-    const R Op = R(3) * w * cF + mt * w * ev.xo[p];
+    const int wc = wclass<Q>(p);
+    const R Ea = cc.w9J[wc] * cPc - cc.w3J[wc] * ev.tr + cc.iwm[wc] * ev.xe[p];
+    const R Oa = (R(3) * lat_w<Q, R>(p)) * cF + cc.iwm[wc] * ev.xo[p];
 #pragma unroll
-    for (int i = 0; i < D; i++) acc[i] += Mp[p][i] * Ep + Dk[p][i] * Op;
+    for (int i = 0; i < D; i++) acc[i] += k.M[p][i] * Ea + k.Dk[p][i] * Oa;
   }
 #pragma unroll
   for (int i = 0; i < D; i++) Pn[i] = Pb[i] - R(0.5) * acc[i];
 }
 
-// The final evaluation: post-collision deviations dp_a = N'_a - w_a n_ref,
+// N' (as deviations dp_a = N'_a - w_a n_ref) and Phi_new at the same Phi:
 //   N'_a = N_a + Omega_a + deltaN_a, Omega_a = -(N_a - J f^eq_a)/tau (Eqs. 12, 20),
 //   N_a - J f^eq_a = (d_a - w_a mdev) - w_a m x_a,
-// together with Phi_new at the same Phi (as eval_phi computes it).
+// the non-equilibrium part formed first, so that its rounding error is relative
+// to itself and not to the much larger d_a; deltaN_p = E_p + O_p and
+// deltaN_pbar = E_p - O_p as in eval_phi.
 template <int Q, typename R>
 __device__ __forceinline__ void eval_np(const R (&d)[Q], const CellCoef<Q, R> &k,
-                                        const R (&Mp)[Lat<Q>::H + 1][Lat<Q>::D],
-                                        const R (&Dk)[Lat<Q>::H + 1][Lat<Q>::D],
-                                        const R (&U)[Lat<Q>::D], R rho, R h2m, R m, R mdev,
+                                        const CollideConst<Q, R> &cc, const R (&U)[Lat<Q>::D],
                                         const R (&Phi)[Lat<Q>::D], const R (&Pb)[Lat<Q>::D],
-                                        R itau, R cpi, R (&dp)[Q], R (&Pn)[Lat<Q>::D]) {
+                                        R (&dp)[Q], R (&Pn)[Lat<Q>::D]) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   EvalParts<Q, R> ev;
-  eval_parts<Q, R>(k, Mp, U, rho, h2m, Phi, cpi, ev);
+  eval_parts<Q, R>(k, cc, U, Phi, ev);
   R acc[D];
 #pragma unroll
   for (int i = 0; i < D; i++) acc[i] = R(0);
-  const R mt = m * itau;
   {
-    const R w = lat_w<Q, R>(0);
-    const R E0 = R(3) * w * k.J * (-ev.tr);
-    const R neq = (d[0] - w * mdev) - (w * m) * ev.xe[0];
-    dp[0] = d[0] - neq * itau + E0;
+    const R neq = (d[0] - cc.wd[0]) - cc.wm[0] * ev.xe[0];
+    dp[0] = d[0] - cc.itau * neq - cc.w3J[0] * ev.tr;
   }
 #pragma unroll
   for (int p = 1; p <= H; p++) {
     R cF, cPc;
     pair_dots<Q, R>(ev, Phi, p, cF, cPc);
-    const R w = lat_w<Q, R>(p);
-    const R Ep = R(3) * w * k.J * (R(3) * cPc - ev.tr);
-    const R Op = R(3) * w * cF;
-    const R wm = w * m, wd = w * mdev;
-    const R neqp = (d[p] - wd) - wm * (ev.xe[p] + ev.xo[p]);
-    const R neqm = (d[p + H] - wd) - wm * (ev.xe[p] - ev.xo[p]);
-    dp[p] = d[p] - neqp * itau + (Ep + Op);
-    dp[p + H] = d[p + H] - neqm * itau + (Ep - Op);
-    const R Ea = Ep + mt * w * ev.xe[p];
-    const R Oa = Op + mt * w * ev.xo[p];
+    const int wc = wclass<Q>(p);
+    const R Ep = cc.w9J[wc] * cPc - cc.w3J[wc] * ev.tr;
+    const R Op = (R(3) * lat_w<Q, R>(p)) * cF;
+    const R neqp = (d[p] - cc.wd[wc]) - cc.wm[wc] * (ev.xe[p] + ev.xo[p]);
+    const R neqm = (d[p + H] - cc.wd[wc]) - cc.wm[wc] * (ev.xe[p] - ev.xo[p]);
+    dp[p] = d[p] - cc.itau * neqp + (Ep + Op);
+    dp[p + H] = d[p + H] - cc.itau * neqm + (Ep - Op);
+    const R Ea = Ep + cc.iwm[wc] * ev.xe[p];
+    const R Oa = Op + cc.iwm[wc] * ev.xo[p];
 #pragma unroll
-    for (int i = 0; i < D; i++) acc[i] += Mp[p][i] * Ea + Dk[p][i] * Oa;
+    for (int i = 0; i < D; i++) acc[i] += k.M[p][i] * Ea + k.Dk[p][i] * Oa;
   }
 #pragma unroll
   for (int i = 0; i < D; i++) Pn[i] = Pb[i] - R(0.5) * acc[i];
@@ -282,60 +289,67 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
                                              CollideState<Q, R> &st) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   const R epsn = sizeof(R) == 4 ? R(64.0 / 16777216.0) : R(64.0 / 9007199254740992.0);
-  R mdev = R(0);
+  // pair sums s_p = d_p + d_pbar and differences t_p = d_p - d_pbar
+  R sp[H + 1], tp[H + 1];
+  R mdev = d[0];
 #pragma unroll
-  for (int a = 0; a < Q; a++) mdev += d[a];
-  const R m = nref + mdev;
+  for (int p = 1; p <= H; p++) {
+    sp[p] = d[p] + d[p + H];
+    tp[p] = d[p] - d[p + H];
+    mdev += sp[p];
+  }
+  CollideConst<Q, R> cc;
+  cc.mdev = mdev;
+  cc.m = nref + mdev;
   // rho = sum f = sum N / J; rho U = sum c f   (Eqs. 14, 15, 17)
-  st.rho = m / k.J;
-  const R im = R(1) / m;
-  const R h2m = R(0.5) * im;
+  st.rho = cc.m / k.J;
+  const R im = R(1) / cc.m;
+  cc.h2m = R(0.5) * im;
 #pragma unroll
   for (int i = 0; i < D; i++) {
     R s = R(0);
 #pragma unroll
-    for (int a = 1; a < Q; a++) {
-      const int ci = Lat<Q>::c(a, i);
-      if (ci > 0) s += d[a];
-      if (ci < 0) s -= d[a];
+    for (int p = 1; p <= H; p++) {
+      const int ci = Lat<Q>::c(p, i);
+      if (ci > 0) s += tp[p];
+      if (ci < 0) s -= tp[p];
     }
     st.U[i] = s * im;
   }
-  // pair sums and differences of the link coefficients
-  R Mp[H + 1][D], Dk[H + 1][D];
+  cc.itau = R(1) / tau;
+  // -1/2 (1 - 1/(2 tau)) times the 2 of f_p - f_pbar = 2 rho w xo
+  const R cpi = -(R(1) - R(0.5) * cc.itau);
 #pragma unroll
-  for (int i = 0; i < D; i++) Mp[0][i] = Dk[0][i] = R(0);
-#pragma unroll
-  for (int p = 1; p <= H; p++)
-#pragma unroll
-    for (int i = 0; i < D; i++) {
-      Mp[p][i] = k.K[p][i] + k.K[p + H][i];
-      Dk[p][i] = k.K[p][i] - k.K[p + H][i];
-    }
-  const R itau = R(1) / tau;
-  const R cpi = -R(0.5) * (R(1) - R(0.5) * itau);
-  // constant part of J F: body force m G, 1/2 sum_a L_a N_a (L_a = -K_abar) and the
-  // reference part -n_ref sum_a w_a K_a of both sums of Eq. 27. The last is the
-  // largest term and is the same every step, so it is formed without rounding
-  // error from the split coefficient KW + KWL. Pb adds the parts of
-  // -1/2 sum_a K_a N'_a that do not change during the iteration.
+  for (int c = 0; c < 3; c++) {
+    const R w = c == 0 ? lat_w<Q, R>(0) : c == 1 ? lat_w<Q, R>(1) : lat_w<Q, R>(Q == 9 ? 3 : 4);
+    cc.dfw[c] = cpi * st.rho * w;
+    cc.w3J[c] = R(3) * w * k.J;
+    cc.w9J[c] = R(9) * w * k.J;
+    cc.iwm[c] = cc.itau * w * cc.m;
+    cc.wm[c] = w * cc.m;
+    cc.wd[c] = w * mdev;
+  }
+  // constant part of J F: body force m G, 1/2 sum_a L_a N_a (L_a = -K_abar), the
+  // reference part -n_ref sum_a w_a K_a of both sums of Eq. 27 (the largest term,
+  // the same every step: formed without rounding error from the split KW + KWL),
+  // and the parts of -1/2 sum_a K_a N'_a that do not change during the
+  // iteration. Over a pair,
+  //   -1/2 (K_pbar d_p + K_p d_pbar) - 1/2 (1 - 1/tau)(K_p d_p + K_pbar d_pbar)
+  //     = -(2 - 1/tau)/4 M_p s_p + (1/tau)/4 D_p t_p.
   R Pb[D];
+  const R am = -R(0.25) * (R(2) - cc.itau), ad = R(0.25) * cc.itau;
 #pragma unroll
   for (int i = 0; i < D; i++) {
     const R pr = nref * k.Kw[i];
     const R err = two_prod_err(nref, k.Kw[i], pr) + nref * k.KwL[i];
-    R s = m * k.G[i] - err - R(0.5) * itau * mdev * k.Kw[i];
-    R sd = R(0);
+    R s = cc.m * k.G[i] - err - R(0.5) * cc.itau * mdev * k.Kw[i];
 #pragma unroll
-    for (int a = 1; a < Q; a++) {
-      s -= R(0.5) * k.K[lat_opp<Q>(a)][i] * d[a];
-      sd += k.K[a][i] * d[a];
-    }
-    Pb[i] = (s - R(0.5) * (R(1) - itau) * sd) - pr;
+    for (int p = 1; p <= H; p++) s += am * k.M[p][i] * sp[p] + ad * k.Dk[p][i] * tp[p];
+    Pb[i] = s - pr;
   }
   R Phi[D], Pn[D];
 #pragma unroll
-  for (int i = 0; i < D; i++) Phi[i] = CHORD ? m * k.Fr[i] : R(0);
+  for (int i = 0; i < D; i++) Phi[i] = CHORD ? cc.m * k.Fr[i] : R(0);
   st.conv = false;
   int it = 0;
   // correction dF = H (Phi_new - Phi); converged when it is at most
@@ -357,12 +371,12 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
       diff = maxnan(diff, absr(x));
       pmax = maxnan(pmax, absr(Phi[i]));
     }
-    return diff <= maxnan(tol * maxnan(m, pmax), epsn * pmax);
+    return diff <= maxnan(tol * maxnan(cc.m, pmax), epsn * pmax);
   };
   if (!FINAL) {
-    // F only: plain iteration on Phi_new
+    // F only: iteration on Phi_new
     while (it < max_iter) {
-      eval_phi<Q, R>(k, Mp, Dk, st.U, st.rho, h2m, m, Phi, Pb, itau, cpi, Pn);
+      eval_phi<Q, R>(k, cc, st.U, Phi, Pb, Pn);
       it++;
       R dF[D];
       const bool ok = correction(dF);
@@ -377,12 +391,12 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
     // every evaluation also forms N'; the accepted correction is applied to
     // N' by extrapolation
     while (it < max_iter) {
-      eval_np<Q, R>(d, k, Mp, Dk, st.U, st.rho, h2m, m, mdev, Phi, Pb, itau, cpi, dp, Pn);
+      eval_np<Q, R>(d, k, cc, st.U, Phi, Pb, dp, Pn);
       it++;
       R dF[D];
       const bool ok = correction(dF);
       if (ok) {
-        extrapolate<Q, R>(k, st.U, Phi, h2m, dF, itau, dp);
+        extrapolate<Q, R>(k, st.U, Phi, cc.h2m, dF, cc.itau, dp);
 #pragma unroll
         for (int i = 0; i < D; i++) Phi[i] += dF[i];
         st.conv = true;

@@ -319,7 +319,8 @@ struct PackArgs {
 //   L^{il} = -1/2 sum_a w_a K^i_a [h^l_a / tau + 3 c^l_a + 3 (3 c_a.P^l.c_a - tr P^l)]
 // returns H = (I - L)^-1.
 template <int Q>
-__device__ void chord_matrix(const CellCoef<Q, double> &k, double tau, double (&Hm)[Lat<Q>::D][Lat<Q>::D]) {
+__device__ void chord_matrix(const CellCoef<Q, double> &k, const double (&K)[Q][Lat<Q>::D], double tau,
+                             double (&Hm)[Lat<Q>::D][Lat<Q>::D]) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   const double T0 = kT0, itau = 1.0 / tau, cpi = -0.5 * (1.0 - 0.5 * itau);
   double g[D][D], trg = 0.0;
@@ -344,7 +345,7 @@ __device__ void chord_matrix(const CellCoef<Q, double> &k, double tau, double (&
       for (int j = 0; j < D; j++) {
         double s = 0.0;
         for (int p = 1; p <= H; p++)
-          s += lat_w<Q, double>(p) * Lat<Q>::c(p, i) * (k.K[p][j] + k.K[p + H][j]) * h[p][l];
+          s += lat_w<Q, double>(p) * Lat<Q>::c(p, i) * (K[p][j] + K[p + H][j]) * h[p][l];
         P[i][j] = 2.0 * cpi * s;
       }
     double trP = 0.0;
@@ -355,7 +356,7 @@ __device__ void chord_matrix(const CellCoef<Q, double> &k, double tau, double (&
         double cPc = 0.0;
         for (int x = 0; x < D; x++)
           for (int y = 0; y < D; y++) cPc += Lat<Q>::c(a, x) * Lat<Q>::c(a, y) * P[x][y];
-        s += lat_w<Q, double>(a) * k.K[a][i] *
+        s += lat_w<Q, double>(a) * K[a][i] *
              (h[a][l] * itau + 3.0 * Lat<Q>::c(a, l) + 3.0 * (3.0 * cPc - trP));
       }
       L[i][l] = -0.5 * s;
@@ -385,32 +386,39 @@ __device__ void chord_matrix(const CellCoef<Q, double> &k, double tau, double (&
 
 template <int Q, typename R>
 __global__ void k_pack_coef(const PackArgs a, R *coef) {
-  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2;
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
+  constexpr int RS = L::template stride<R>();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.nrec) return;
   const int64_t c = a.plane ? r * a.nfast : r;
-  const int64_t st = a.stride;
-  coef[L::J * st + r] = static_cast<R>(a.J[c]);
+  R *out = coef + r * RS;
+  for (int k = 0; k < RS; k++) out[k] = R(0);
+  out[L::J] = static_cast<R>(a.J[c]);
   for (int i = 0; i < D; i++)
     for (int j = i; j < D; j++)
-      coef[(L::GINV + sym<D>(i, j)) * st + r] =
-          static_cast<R>(a.ginv[c * NS + sym<D>(i, j)] - (i == j ? 1.0 : 0.0));
+      out[L::GINV + sym<D>(i, j)] = static_cast<R>(a.ginv[c * NS + sym<D>(i, j)] - (i == j ? 1.0 : 0.0));
   for (int i = 0; i < D; i++) {
     double s = 0.0;
     for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];  // G^i = G . g^i
-    coef[(L::BODY + i) * st + r] = static_cast<R>(s);
+    out[L::BODY + i] = static_cast<R>(s);
   }
-  for (int av = 1; av < Q; av++)
-    for (int i = 0; i < D; i++)
-      coef[(L::K + (av - 1) * D + i) * st + r] = static_cast<R>(a.K[(c * Q + av) * D + i]);
-  // reference-state part of J F: sum_a w_a K^i_a
+  double K[Q][D];
+  for (int av = 0; av < Q; av++)
+    for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
+  // pair sums and differences of the link coefficients, formed in FP64
+  for (int p = 1; p <= H; p++)
+    for (int i = 0; i < D; i++) {
+      out[L::MP + (p - 1) * D + i] = static_cast<R>(K[p][i] + K[p + H][i]);
+      out[L::DK + (p - 1) * D + i] = static_cast<R>(K[p][i] - K[p + H][i]);
+    }
+  // reference-state part of J F: sum_a w_a K^i_a, as a hi/lo pair
   for (int i = 0; i < D; i++) {
     double s = 0.0;
-    for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * a.K[(c * Q + av) * D + i];
+    for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * K[av][i];
     const R hi = static_cast<R>(s);
-    coef[(L::KW + i) * st + r] = hi;
-    coef[(L::KWL + i) * st + r] = static_cast<R>(s - static_cast<double>(hi));
+    out[L::KW + i] = hi;
+    out[L::KWL + i] = static_cast<R>(s - static_cast<double>(hi));
   }
   // chord matrix and rest-state force
   {
@@ -424,32 +432,29 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
       k.G[i] = s;
       k.KwL[i] = 0.0;
       k.Fr[i] = 0.0;
+      double w = 0.0;
+      for (int av = 1; av < Q; av++) w += lat_w<Q, double>(av) * K[av][i];
+      k.Kw[i] = w;
       for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
     }
-    for (int av = 0; av < Q; av++)
-      for (int i = 0; i < D; i++) k.K[av][i] = a.K[(c * Q + av) * D + i];
-    for (int i = 0; i < D; i++) {
-      double s = 0.0;
-      for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * k.K[av][i];
-      k.Kw[i] = s;  // sum_a w_a K_a
-    }
+    pairs_from_K<Q, double>(K, k);
     double Hm[D][D];
-    chord_matrix<Q>(k, a.tau, Hm);
+    chord_matrix<Q>(k, K, a.tau, Hm);
     for (int i = 0; i < D; i++)
-      for (int j = 0; j < D; j++) coef[(L::HM + i * D + j) * st + r] = static_cast<R>(Hm[i][j]);
+      for (int j = 0; j < D; j++) out[L::HM + i * D + j] = static_cast<R>(Hm[i][j]);
     // F at rest (rho = 1, U = 0), the start value of the chord iteration
     double N[Q], U0[D];
     for (int i = 0; i < D; i++) U0[i] = 0.0;
     EqParts<Q, double> e;
     eq_parts<Q, double>(k.gd, U0, U0, e);
     for (int av = 0; av < Q; av++) {
-      const int p = av <= Lat<Q>::H ? av : av - Lat<Q>::H;
+      const int p = av <= H ? av : av - H;
       N[av] = k.J * lat_w<Q, double>(av) * eq_even<Q, double>(e, p);
     }
     double Np[Q];
     CollideState<Q, double> cs;
     collide_cell<Q, double, false, false>(N, k, 0.0, a.tau, 1e-15, 400, Np, cs);
-    for (int i = 0; i < D; i++) coef[(L::FR + i) * st + r] = static_cast<R>(cs.conv ? cs.F[i] : 0.0);
+    for (int i = 0; i < D; i++) out[L::FR + i] = static_cast<R>(cs.conv ? cs.F[i] : 0.0);
   }
   // wall velocity: rigid motion of the adjacent wall, at the point halfway to the ghost node
   const Addr<Q> ad(a.g, c);
@@ -475,7 +480,7 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
     }
     break;
   }
-  for (int i = 0; i < D; i++) coef[(L::UW + i) * st + r] = static_cast<R>(uw[i]);
+  for (int i = 0; i < D; i++) out[L::UW + i] = static_cast<R>(uw[i]);
 }
 
 template <int Q>
@@ -489,7 +494,7 @@ static cudaError_t pack_q(const vlb_sim *sim, cudaStream_t s) {
   a.ginv = m->d_ginv;
   a.K = m->d_K;
   a.nrec = sim->ncoef;
-  a.stride = sim->ncoef;
+  a.stride = 0;
   a.nfast = m->md.n[m->md.dim - 1];
   a.plane = sim->plane;
   a.tau = sim->p.tau;

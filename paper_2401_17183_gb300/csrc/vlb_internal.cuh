@@ -71,37 +71,59 @@ __host__ __device__ constexpr int sym(int i, int j) {
 }
 
 // --------------------------------------------------------------------------
-// Coefficient record of one cell (or one column in plane mode), structure of
-// arrays: value k of record r lives at coef[k * stride + r].
+// Coefficient record of one cell (or one column in plane mode). Records are
+// stored one after another (record r at coef + r * RS) and padded to a
+// multiple of 16 bytes, so a thread reads its record with 16-byte vector
+// loads from one base address. Link coefficients are stored per pair
+// (p, pbar = p + H) as M_p = K_p + K_pbar and D_p = K_p - K_pbar.
 template <int Q>
 struct CoefLayout {
-  static constexpr int D = Lat<Q>::D;
+  static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   static constexpr int NS = D * (D + 1) / 2;
   static constexpr int J = 0;                  // J (Eq. 5)
   static constexpr int GINV = 1;               // g^ij - delta^ij packed (Eq. 8)
   static constexpr int BODY = GINV + NS;       // G^i = G . g^i
-  static constexpr int K = BODY + D;           // K^i_a, a = 1..Q-1: K + (a-1)*D + i
-  static constexpr int KW = K + (Q - 1) * D;   // sum_a w_a K^i_a (reference-state part of J F)
+  static constexpr int KW = BODY + D;          // sum_a w_a K^i_a (reference-state part of J F)
   static constexpr int KWL = KW + D;           // its low part: KW + KWL = the FP64 value
   static constexpr int HM = KWL + D;           // chord matrix (I - L)^-1, row-major D x D
   static constexpr int FR = HM + D * D;        // F of the rest state at rho = 1 (start value)
   static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
-  static constexpr int NC = UW + D;
+  static constexpr int MP = UW + D;            // M_p^i, p = 1..H: MP + (p-1)*D + i
+  static constexpr int DK = MP + H * D;        // D_p^i
+  static constexpr int NC = DK + H * D;
+  // record stride in elements of type R (16-byte multiple)
+  template <typename R>
+  static constexpr int stride() {
+    return (NC + (int)(16 / sizeof(R)) - 1) / (int)(16 / sizeof(R)) * (int)(16 / sizeof(R));
+  }
 };
 
 // Per-cell coefficients held in registers during a collision.
 template <int Q, typename R>
 struct CellCoef {
-  static constexpr int D = Lat<Q>::D;
+  static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   R J;
   R gd[D * (D + 1) / 2];  // g^ij - delta^ij: stored as a deviation so that rounding is
                           // relative to the (small) departure from a uniform lattice
   R G[D];
-  R K[Q][D];   // K[0] = 0
   R Kw[D], KwL[D];
   R Hm[D][D];
   R Fr[D];
+  R M[H + 1][D];   // K_p + K_pbar (index 0 unused, zero)
+  R Dk[H + 1][D];  // K_p - K_pbar
 };
+
+// pair sums and differences from per-direction link coefficients K[a][i]
+template <int Q, typename R, typename KT>
+__host__ __device__ __forceinline__ void pairs_from_K(const KT &K, CellCoef<Q, R> &k) {
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  for (int i = 0; i < D; i++) k.M[0][i] = k.Dk[0][i] = R(0);
+  for (int p = 1; p <= H; p++)
+    for (int i = 0; i < D; i++) {
+      k.M[p][i] = R(K[p][i] + K[p + H][i]);
+      k.Dk[p][i] = R(K[p][i] - K[p + H][i]);
+    }
+}
 
 constexpr double kT0 = 1.0 / 3.0;
 

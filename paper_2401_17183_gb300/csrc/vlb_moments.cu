@@ -73,11 +73,13 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
       k.Fr[i] = 0.0;
       for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
     }
+    double K[Q][D];
     for (int av = 0; av < Q; av++)
-      for (int i = 0; i < D; i++) k.K[av][i] = a.K[(c * Q + av) * D + i];
+      for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
+    pairs_from_K<Q, double>(K, k);
     for (int i = 0; i < D; i++) {
       double s = 0.0;
-      for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * k.K[av][i];
+      for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * K[av][i];
       k.Kw[i] = s;  // sum_a w_a K_a
     }
     double Np[Q];

@@ -39,6 +39,33 @@ struct StepArgs {
 // index type: 32-bit whenever q * ncell fits.
 constexpr int kStepThreads = 128;
 
+// read RS values of type R from a 16-byte aligned record with vector loads
+// through the read-only path
+template <typename R, int RS>
+__device__ __forceinline__ void load_record(const R *__restrict__ p, R (&out)[RS]) {
+  if constexpr (sizeof(R) == 4) {
+    static_assert(RS % 4 == 0, "record stride must be a multiple of 16 bytes");
+    const float4 *v = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < RS / 4; i++) {
+      const float4 x = __ldg(v + i);
+      out[4 * i] = x.x;
+      out[4 * i + 1] = x.y;
+      out[4 * i + 2] = x.z;
+      out[4 * i + 3] = x.w;
+    }
+  } else {
+    static_assert(RS % 2 == 0, "record stride must be a multiple of 16 bytes");
+    const double2 *v = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < RS / 2; i++) {
+      const double2 x = __ldg(v + i);
+      out[2 * i] = x.x;
+      out[2 * i + 1] = x.y;
+    }
+  }
+}
+
 template <int Q, typename S, typename R, bool ODD, typename IT>
 __global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? 3 : 1) k_step(const StepArgs a) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
@@ -58,29 +85,33 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? 3 : 1) k_step(c
   pull<Q, ODD, S, R, IT>(f, ps, ad, N);
 
   // ---- coefficients: one record per column of the fastest axis (plane mode)
-  // or per cell
+  // or per cell, read with 16-byte vector loads
   const IT rec = a.plane ? (D == 3 ? (IT)blockIdx.z * (IT)a.g.n[1] + (IT)blockIdx.y : (IT)blockIdx.y)
                          : cell;
-  const IT cs = (IT)a.cstride;
-  const R *__restrict__ cr = coef + rec;
+  constexpr int RS = L::template stride<R>();
+  R rv[RS];
+  load_record<R, RS>(coef + (int64_t)rec * RS, rv);
   CellCoef<Q, R> k;
-  k.J = __ldg(cr + L::J * cs);
+  k.J = rv[L::J];
 #pragma unroll
-  for (int i = 0; i < L::NS; i++) k.gd[i] = __ldg(cr + (L::GINV + i) * cs);
+  for (int i = 0; i < L::NS; i++) k.gd[i] = rv[L::GINV + i];
 #pragma unroll
   for (int i = 0; i < D; i++) {
-    k.G[i] = __ldg(cr + (L::BODY + i) * cs);
-    k.Kw[i] = __ldg(cr + (L::KW + i) * cs);
-    k.KwL[i] = __ldg(cr + (L::KWL + i) * cs);
-    k.Fr[i] = __ldg(cr + (L::FR + i) * cs);
-    k.K[0][i] = R(0);
+    k.G[i] = rv[L::BODY + i];
+    k.Kw[i] = rv[L::KW + i];
+    k.KwL[i] = rv[L::KWL + i];
+    k.Fr[i] = rv[L::FR + i];
+    k.M[0][i] = k.Dk[0][i] = R(0);
 #pragma unroll
-    for (int j = 0; j < D; j++) k.Hm[i][j] = __ldg(cr + (L::HM + i * D + j) * cs);
+    for (int j = 0; j < D; j++) k.Hm[i][j] = rv[L::HM + i * D + j];
   }
 #pragma unroll
-  for (int av = 1; av < Q; av++)
+  for (int p = 1; p <= H; p++)
 #pragma unroll
-    for (int i = 0; i < D; i++) k.K[av][i] = __ldg(cr + (L::K + (av - 1) * D + i) * cs);
+    for (int i = 0; i < D; i++) {
+      k.M[p][i] = rv[L::MP + (p - 1) * D + i];
+      k.Dk[p][i] = rv[L::DK + (p - 1) * D + i];
+    }
 
   // ---- collide (section 2.2)
   R Np[Q];
@@ -93,7 +124,7 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(R) == 4 ? 3 : 1) k_step(c
   const bool moving = a.moving && ad.wall_cell();
   R uw[D];
 #pragma unroll
-  for (int i = 0; i < D; i++) uw[i] = moving ? __ldg(cr + (L::UW + i) * cs) : R(0);
+  for (int i = 0; i < D; i++) uw[i] = moving ? rv[L::UW + i] : R(0);
   EqParts<Q, R> ew;
   if (moving) {
     R zero[D];
@@ -147,7 +178,7 @@ static cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
   dim3 grid((unsigned)((nfast + kStepThreads - 1) / kStepThreads),
             (unsigned)(dim == 3 ? m->md.n[1] : m->md.n[0]), (unsigned)(dim == 3 ? m->md.n[0] : 1));
   // 32-bit indexing when every population offset fits
-  const bool i32 = (int64_t)Q * m->ncell < ((int64_t)1 << 31) && sim->ncoef * (int64_t)sim->nc < ((int64_t)1 << 31);
+  const bool i32 = (int64_t)Q * m->ncell < ((int64_t)1 << 31);
   if (i32) {
     if (odd)
       k_step<Q, S, R, true, int32_t><<<grid, kStepThreads, 0, s>>>(a);
