@@ -2,20 +2,36 @@
 // moments (Eqs. 14, 15, 17), the implicit inertial force F (Eq. 27, with
 // deltaPi of Eq. 30 and deltaN of Eq. 31), the curvilinear equilibrium
 // (Eq. 33) with U~ = U + F/(2 rho), and the BGK post-collision populations
-// N' = N + Omega + deltaN (Eqs. 12, 20). Shared by the step and moments kernels.
+// N' = N + Omega + deltaN (Eqs. 12, 20). Shared by the step, moments and
+// coefficient-packing kernels.
 //
 // Populations enter and leave as deviations d_a = N_a - w_a n_ref from a
 // uniform reference n_ref = rho_0 J_ref (n_ref = 0 gives plain populations).
 // The reference is the same in every cell, so advection and bounce-back move
 // deviations exactly as they move populations, while every product below
 // works on small numbers: that keeps FP32 rounding relative to the deviation,
-// not to N. The force is carried as Phi = J F, which keeps J out of every
-// product formed once per step with the same operands.
+// not to N. The force is carried as Phi = J F.
 //
 // Directions come in pairs (p, pbar = p + H) with c_pbar = -c_p; every sum over
-// directions below is a sum over pairs of an even part (same for p and pbar)
-// and an odd part (opposite signs), with the link coefficients stored as
+// directions is a sum over pairs of an even part (same for p and pbar) and an
+// odd part (opposite signs), with the link coefficients stored as
 // M_p = K_p + K_pbar and D_p = K_p - K_pbar.
+//
+// The map Phi -> Phi_new of Eq. 27 is evaluated in a reduced form. Writing
+//   N'_a - w_a n_ref = (1 - 1/tau) d_a + w_a (mdev + m x_a)/tau + deltaN_a,
+// with J f^eq_a = w_a m (1 + x_a) and x_p = xe_p + xo_p, x_pbar = xe_p - xo_p,
+// deltaN_p = E_p + O_p, deltaN_pbar = E_p - O_p (Eq. 31, 1/T0 = 3),
+//   E_p = 3 w_p J (3 c_p.S.c_p - tr S),  O_p = 3 w_p c_p.Phi,
+// S the symmetric part of deltaPi (Eq. 30), linear in the xo_q, gives
+//   Phi_new = Pb - 1/2 { m [sum_p Ae_p xe_p + sum_p Ao_p xo_p] + T Phi },
+// where Pb holds everything fixed during the iteration. Because xe_p is
+// linear in B = gd T0 + U~ U~ and xo_p linear in U and in C^kkl (k != l),
+// the pair sums collapse into a polynomial in U~ with per-cell constant
+// coefficients (build_record):
+//   Phi_new = Pb' - 1/2 { m [PE : U~U~ + PO2 : (U~^k)^2 U~^l + LO U~] + TL Phi },
+//   Pb' = Pb - 1/2 m (CE + PO1 U).
+// The post-collision populations themselves are formed once, at the converged
+// Phi, direction by direction.
 #pragma once
 
 #include "vlb_internal.cuh"
@@ -32,262 +48,247 @@ struct CollideState {
   bool conv;
 };
 
-// Direction-independent part of one evaluation for a given Phi: the
-// equilibrium of Eq. 33 as J f^eq_a = w_a m (1 + x_a), x_p = xe_p + xo_p,
-// x_pbar = xe_p - xo_p (only x is formed, never 1 + x), and deltaPi of Eq. 30
-// with its trace.
-template <int Q, typename R>
-struct EvalParts {
-  static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  R xe[H + 1], xo[H + 1];
-  R dP[D][D];
-  R tr;
-};
+// D x D inverse (D = 2 or 3) by cofactors, FP64
+template <int D>
+__device__ void inverse_small(const double (&A)[D][D], double (&X)[D][D]) {
+  if (D == 2) {
+    const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    X[0][0] = A[1][1] / det;
+    X[0][1] = -A[0][1] / det;
+    X[1][0] = -A[1][0] / det;
+    X[1][1] = A[0][0] / det;
+  } else {
+    double C[D][D];
+    for (int i = 0; i < D; i++)
+      for (int j = 0; j < D; j++) {
+        const int i1 = (i + 1) % D, i2 = (i + 2) % D, j1 = (j + 1) % D, j2 = (j + 2) % D;
+        C[i][j] = A[i1][j1] * A[i2][j2] - A[i1][j2] * A[i2][j1];
+      }
+    double det = 0.0;
+    for (int j = 0; j < D; j++) det += A[0][j] * C[0][j];
+    for (int i = 0; i < D; i++)
+      for (int j = 0; j < D; j++) X[i][j] = C[j][i] / det;
+  }
+}
 
-// weight class of a direction: 0 rest, 1 axis, 2 diagonal
+// Coefficient record of one cell in FP64 from its geometry: J, g^ij (packed),
+// G^i = G . g^i and the link coefficients K^i_a (Eq. 25). Every entry is
+// filled except FR and UW, which are left zero. With itau = 1/tau,
+// cpi = -(1 - itau/2) and the pair sums over p = 1..H:
+//   R^i_kl  = sum_p w_p M^i_p (3 c^k_p c^l_p - delta_kl)
+//   Ao^i_p  = w_p [itau D^i_p + 3 cpi c_p.R^i.M_p]    (xo_p: BGK part and, via S, E_p)
+//   PE^i_kl = (3/2) itau R^i_kl                        (xe_p: BGK part)
+//   PO1^i_l = 3 sum_p Ao^i_p c^l_p
+//   PO2^i_kl = (9/2) sum_p Ao^i_p c^l_p (3 (c^k_p)^2 - 1),  k != l
+//   TT^i_j  = 3 sum_p w_p D^i_p c^j_p                  (O_p)
+//   LO^i_j  = T0 [sum_{k != j} PO2^i_kj gd_kk + 2 sum_{l != j} PO2^i_jl gd_jl]
+//   LD^i_j  = T0 sum_{k != j} PO2^i_kj,   TL = TT + LD / 2
+//   CE^i    = T0 sum_kl PE^i_kl gd_kl
+// and the chord matrix (I - L)^-1 with L = -(LO/4 + TL/2), the part of the
+// Jacobian of the map that stays when U -> 0. PE is stored packed over
+// k <= l with the off-diagonal entries doubled (U~U~ is symmetric).
 template <int Q>
-__host__ __device__ constexpr int wclass(int a) {
-  return a == 0 ? 0 : lat_nnz<Q>(a) == 1 ? 1 : 2;
-}
-
-// Per-cell constants of one collision.
-template <int Q, typename R>
-struct CollideConst {
-  R m, mdev, h2m, itau;
-  R dfw[3];   // -(1 - 1/(2 tau)) rho w, per weight class
-  R w9J[3];   // 9 w J
-  R w3J[3];   // 3 w J
-  R iwm[3];   // w m / tau
-  R wm[3];    // w m
-  R wd[3];    // w mdev
-};
-
-template <int Q, typename R>
-__device__ __forceinline__ void eval_parts(const CellCoef<Q, R> &k, const CollideConst<Q, R> &cc,
-                                           const R (&U)[Lat<Q>::D], const R (&Phi)[Lat<Q>::D],
-                                           EvalParts<Q, R> &ev) {
-  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  R dU[D];
-#pragma unroll
-  for (int i = 0; i < D; i++) dU[i] = Phi[i] * cc.h2m;
-  EqParts<Q, R> e;
-  eq_parts<Q, R>(k.gd, U, dU, e);
-  ev.xe[0] = eq_even_dev<Q, R>(e, 0);
-  ev.xo[0] = R(0);
-#pragma unroll
-  for (int p = 1; p <= H; p++) {
-    ev.xe[p] = eq_even_dev<Q, R>(e, p);
-    ev.xo[p] = eq_odd<Q, R>(e, U, p);
-  }
-  // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a - L^j_a) f^eq_a   (Eq. 30):
-  // K_a - L_a = K_a + K_abar = M_p, a pair contributes c_p (f_p - f_pbar) with
-  // f_p - f_pbar = 2 rho w_p xo_p
-#pragma unroll
+__device__ void build_record(double J, const double *ginv, const double *G,
+                             const double (&K)[Q][Lat<Q>::D], double tau, double *rec) {
+  using L = CoefLayout<Q>;
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H, NS = L::NS;
+  const double T0 = kT0, itau = 1.0 / tau, cpi = -(1.0 - 0.5 * itau);
+  for (int k = 0; k < L::NC; k++) rec[k] = 0.0;
+  rec[L::J] = J;
+  double gd[D][D];
   for (int i = 0; i < D; i++)
-#pragma unroll
-    for (int j = 0; j < D; j++) ev.dP[i][j] = R(0);
-#pragma unroll
+    for (int j = 0; j < D; j++) gd[i][j] = ginv[sym<D>(i, j)] - (i == j ? 1.0 : 0.0);
+  for (int i = 0; i < D; i++)
+    for (int j = i; j < D; j++) rec[L::GINV + sym<D>(i, j)] = gd[i][j];
+  for (int i = 0; i < D; i++) {
+    rec[L::BODY + i] = G[i];
+    double s = 0.0;
+    for (int a = 1; a < Q; a++) s += lat_w<Q, double>(a) * K[a][i];
+    rec[L::KW + i] = s;
+  }
+  double M[H + 1][D], Dk[H + 1][D], c[H + 1][D], w[H + 1];
   for (int p = 1; p <= H; p++) {
-    const R df = cc.dfw[wclass<Q>(p)] * ev.xo[p];
-    R t[D];
-#pragma unroll
-    for (int j = 0; j < D; j++) t[j] = k.M[p][j] * df;
-#pragma unroll
+    w[p] = lat_w<Q, double>(p);
     for (int i = 0; i < D; i++) {
-      const int ci = Lat<Q>::c(p, i);
-      if (ci == 0) continue;
-#pragma unroll
-      for (int j = 0; j < D; j++) {
-        if (ci > 0)
-          ev.dP[i][j] += t[j];
-        else
-          ev.dP[i][j] -= t[j];
-      }
+      M[p][i] = K[p][i] + K[p + H][i];
+      Dk[p][i] = K[p][i] - K[p + H][i];
+      c[p][i] = Lat<Q>::c(p, i);
+      rec[L::MP + (p - 1) * D + i] = M[p][i];
+      rec[L::DK + (p - 1) * D + i] = Dk[p][i];
     }
   }
-  ev.tr = R(0);
-#pragma unroll
-  for (int i = 0; i < D; i++) ev.tr += ev.dP[i][i];
-}
-
-// c_p.Phi and c_p.dPi.c_p for the positive direction p of a pair
-template <int Q, typename R>
-__device__ __forceinline__ void pair_dots(const EvalParts<Q, R> &ev, const R (&Phi)[Lat<Q>::D], int p,
-                                          R &cF, R &cPc) {
-  constexpr int D = Lat<Q>::D;
-  cF = R(0);
-  cPc = R(0);
-#pragma unroll
+  double Rt[D][D][D];
+  for (int i = 0; i < D; i++)
+    for (int k = 0; k < D; k++)
+      for (int l = 0; l < D; l++) {
+        double s = 0.0;
+        for (int p = 1; p <= H; p++)
+          s += w[p] * M[p][i] * (3.0 * c[p][k] * c[p][l] - (k == l ? 1.0 : 0.0));
+        Rt[i][k][l] = s;
+      }
+  double Ao[H + 1][D];
+  for (int p = 1; p <= H; p++)
+    for (int i = 0; i < D; i++) {
+      double cRM = 0.0;
+      for (int k = 0; k < D; k++)
+        for (int l = 0; l < D; l++) cRM += c[p][k] * Rt[i][k][l] * M[p][l];
+      Ao[p][i] = w[p] * (itau * Dk[p][i] + 3.0 * cpi * cRM);
+    }
+  double PO2[D][D][D];  // [i][k][l]
+  double LO[D][D], TL[D][D];
   for (int i = 0; i < D; i++) {
-    const int ci = Lat<Q>::c(p, i);
-    if (ci == 0) continue;
-    if (ci > 0)
-      cF += Phi[i];
-    else
-      cF -= Phi[i];
-#pragma unroll
+    double ce = 0.0;
+    for (int k = 0; k < D; k++)
+      for (int l = 0; l < D; l++) {
+        const double pe = 1.5 * itau * Rt[i][k][l];
+        ce += T0 * pe * gd[k][l];
+        if (k <= l) rec[L::PE + i * NS + sym<D>(k, l)] = (k == l ? 1.0 : 2.0) * pe;
+      }
+    rec[L::CE + i] = ce;
+    for (int l = 0; l < D; l++) {
+      double s = 0.0;
+      for (int p = 1; p <= H; p++) s += Ao[p][i] * c[p][l];
+      rec[L::PO1 + i * D + l] = 3.0 * s;
+    }
+    for (int k = 0; k < D; k++)
+      for (int l = 0; l < D; l++) {
+        PO2[i][k][l] = 0.0;
+        if (k == l) continue;
+        double s = 0.0;
+        for (int p = 1; p <= H; p++) s += Ao[p][i] * c[p][l] * (3.0 * c[p][k] * c[p][k] - 1.0);
+        PO2[i][k][l] = 4.5 * s;
+        rec[L::PO2 + i * L::NO + offd<D>(k, l)] = PO2[i][k][l];
+      }
+  }
+  for (int i = 0; i < D; i++)
     for (int j = 0; j < D; j++) {
-      const int cj = Lat<Q>::c(p, j);
-      if (cj == 0) continue;
-      if (ci * cj > 0)
-        cPc += ev.dP[i][j];
-      else
-        cPc -= ev.dP[i][j];
-    }
-  }
-}
-
-// Phi_new = J F_new (Eq. 27 plus the body force) for a given Phi without
-// forming N'. With
-//   N'_a - w_a n_ref = (1 - 1/tau) d_a + (w_a mdev + w_a m x_a)/tau + deltaN_a
-// and deltaN_p = E_p + O_p, deltaN_pbar = E_p - O_p (Eq. 31, 1/T0 = 3),
-//   E_p = 3 w_p J (3 c_p.dPi.c_p - tr dPi),  O_p = 3 w_p c_p.Phi,
-// the sum -1/2 sum_a K_a (N'_a - w_a n_ref) is the cell constant Pb plus
-//   -1/2 sum_p [M_p (E_p + w_p m xe_p / tau) + D_p (O_p + w_p m xo_p / tau)].
-template <int Q, typename R>
-__device__ __forceinline__ void eval_phi(const CellCoef<Q, R> &k, const CollideConst<Q, R> &cc,
-                                         const R (&U)[Lat<Q>::D], const R (&Phi)[Lat<Q>::D],
-                                         const R (&Pb)[Lat<Q>::D], R (&Pn)[Lat<Q>::D]) {
-  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  EvalParts<Q, R> ev;
-  eval_parts<Q, R>(k, cc, U, Phi, ev);
-  R acc[D];
-#pragma unroll
-  for (int i = 0; i < D; i++) acc[i] = R(0);
-#pragma unroll
-  for (int p = 1; p <= H; p++) {
-    R cF, cPc;
-    pair_dots<Q, R>(ev, Phi, p, cF, cPc);
-    const int wc = wclass<Q>(p);
-    const R Ea = cc.w9J[wc] * cPc - cc.w3J[wc] * ev.tr + cc.iwm[wc] * ev.xe[p];
-    const R Oa = (R(3) * lat_w<Q, R>(p)) * cF + cc.iwm[wc] * ev.xo[p];
-#pragma unroll
-    for (int i = 0; i < D; i++) acc[i] += k.M[p][i] * Ea + k.Dk[p][i] * Oa;
-  }
-#pragma unroll
-  for (int i = 0; i < D; i++) Pn[i] = Pb[i] - R(0.5) * acc[i];
-}
-
-// N' (as deviations dp_a = N'_a - w_a n_ref) and Phi_new at the same Phi:
-//   N'_a = N_a + Omega_a + deltaN_a, Omega_a = -(N_a - J f^eq_a)/tau (Eqs. 12, 20),
-//   N_a - J f^eq_a = (d_a - w_a mdev) - w_a m x_a,
-// the non-equilibrium part formed first, so that its rounding error is relative
-// to itself and not to the much larger d_a; deltaN_p = E_p + O_p and
-// deltaN_pbar = E_p - O_p as in eval_phi.
-template <int Q, typename R>
-__device__ __forceinline__ void eval_np(const R (&d)[Q], const CellCoef<Q, R> &k,
-                                        const CollideConst<Q, R> &cc, const R (&U)[Lat<Q>::D],
-                                        const R (&Phi)[Lat<Q>::D], const R (&Pb)[Lat<Q>::D],
-                                        R (&dp)[Q], R (&Pn)[Lat<Q>::D]) {
-  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  EvalParts<Q, R> ev;
-  eval_parts<Q, R>(k, cc, U, Phi, ev);
-  R acc[D];
-#pragma unroll
-  for (int i = 0; i < D; i++) acc[i] = R(0);
-  {
-    const R neq = (d[0] - cc.wd[0]) - cc.wm[0] * ev.xe[0];
-    dp[0] = d[0] - cc.itau * neq - cc.w3J[0] * ev.tr;
-  }
-#pragma unroll
-  for (int p = 1; p <= H; p++) {
-    R cF, cPc;
-    pair_dots<Q, R>(ev, Phi, p, cF, cPc);
-    const int wc = wclass<Q>(p);
-    const R Ep = cc.w9J[wc] * cPc - cc.w3J[wc] * ev.tr;
-    const R Op = (R(3) * lat_w<Q, R>(p)) * cF;
-    const R neqp = (d[p] - cc.wd[wc]) - cc.wm[wc] * (ev.xe[p] + ev.xo[p]);
-    const R neqm = (d[p + H] - cc.wd[wc]) - cc.wm[wc] * (ev.xe[p] - ev.xo[p]);
-    dp[p] = d[p] - cc.itau * neqp + (Ep + Op);
-    dp[p + H] = d[p + H] - cc.itau * neqm + (Ep - Op);
-    const R Ea = Ep + cc.iwm[wc] * ev.xe[p];
-    const R Oa = Op + cc.iwm[wc] * ev.xo[p];
-#pragma unroll
-    for (int i = 0; i < D; i++) acc[i] += k.M[p][i] * Ea + k.Dk[p][i] * Oa;
-  }
-#pragma unroll
-  for (int i = 0; i < D; i++) Pn[i] = Pb[i] - R(0.5) * acc[i];
-}
-
-// First-order move of dp from Phi to Phi + dPhi. With U~ = U + Phi/(2m):
-//   d dp_a / dPhi . dPhi = (w_a / (2 tau)) dx_a/dU~ . dPhi + 3 w_a c_a . dPhi
-// where dx_a/dU~ takes the U~ U~ terms of B (even in c_a) and the g^ij U~
-// terms of C (odd in c_a):
-//   even: 9 (c.U~)(c.dPhi) - 3 U~.dPhi
-//   odd : 9/2 [(c.g.c)(c.dPhi) - T0 (2 c.g.dPhi + tr(g) c.dPhi)]
-// The terms left out (the cubic U~ U~ U~ part and deltaPi) are of order |U|^2
-// and Theta^2 relative to these, so for the small last correction of the
-// chord iteration this leaves an error far below the FP32 unit roundoff.
-template <int Q, typename R>
-__device__ __forceinline__ void extrapolate(const CellCoef<Q, R> &k, const R (&U)[Lat<Q>::D],
-                                            const R (&Phi)[Lat<Q>::D], R h2m,
-                                            const R (&dPhi)[Lat<Q>::D], R itau, R (&dp)[Q]) {
-  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  R Ut[D], gD[D], trg = R(D), UD = R(0);
-#pragma unroll
-  for (int i = 0; i < D; i++) Ut[i] = U[i] + Phi[i] * h2m;
-#pragma unroll
-  for (int i = 0; i < D; i++) {
-    R s = dPhi[i];
-#pragma unroll
-    for (int j = 0; j < D; j++) s += k.gd[sym<D>(i, j)] * dPhi[j];
-    gD[i] = s;  // g . dPhi
-    trg += k.gd[sym<D>(i, i)];
-    UD += Ut[i] * dPhi[i];
-  }
-  const R ht = R(0.5) * itau;
-  dp[0] += ht * lat_w<Q, R>(0) * (-R(3) * UD);
-#pragma unroll
-  for (int p = 1; p <= H; p++) {
-    R cD = R(0), cU = R(0), cgD = R(0), cgc = R(0);
-#pragma unroll
-    for (int i = 0; i < D; i++) {
-      const int ci = Lat<Q>::c(p, i);
-      if (ci == 0) continue;
-      cD += ci > 0 ? dPhi[i] : -dPhi[i];
-      cU += ci > 0 ? Ut[i] : -Ut[i];
-      cgD += ci > 0 ? gD[i] : -gD[i];
-      cgc += R(1);
-#pragma unroll
-      for (int j = 0; j < D; j++) {
-        const int cj = Lat<Q>::c(p, j);
-        if (cj == 0) continue;
-        cgc += ci * cj > 0 ? k.gd[sym<D>(i, j)] : -k.gd[sym<D>(i, j)];
+      double tt = 0.0;
+      for (int p = 1; p <= H; p++) tt += 3.0 * w[p] * Dk[p][i] * c[p][j];
+      double lo = 0.0, ld = 0.0;
+      for (int k = 0; k < D; k++) {
+        if (k == j) continue;
+        lo += T0 * (PO2[i][k][j] * gd[k][k] + 2.0 * PO2[i][j][k] * gd[j][k]);
+        ld += T0 * PO2[i][k][j];
       }
+      LO[i][j] = lo;
+      TL[i][j] = tt + 0.5 * ld;
+      rec[L::LO + i * D + j] = lo;
+      rec[L::TL + i * D + j] = TL[i][j];
     }
-    const R w = lat_w<Q, R>(p);
-    const R ev = ht * w * (R(9) * cU * cD - R(3) * UD);
-    const R od = ht * w * R(4.5) * (cgc * cD - R(kT0) * (R(2) * cgD + trg * cD)) + R(3) * w * cD;
-    dp[p] += ev + od;
-    dp[p + H] += ev - od;
-  }
+  double A[D][D], Hm[D][D];
+  for (int i = 0; i < D; i++)
+    for (int j = 0; j < D; j++) A[i][j] = (i == j ? 1.0 : 0.0) + 0.25 * LO[i][j] + 0.5 * TL[i][j];
+  inverse_small<D>(A, Hm);
+  for (int i = 0; i < D; i++)
+    for (int j = 0; j < D; j++) rec[L::HM + i * D + j] = Hm[i][j];
 }
 
 // x y = p + e exactly (FMA two-product)
 __device__ __forceinline__ float two_prod_err(float x, float y, float p) { return fmaf(x, y, -p); }
 __device__ __forceinline__ double two_prod_err(double x, double y, double p) { return fma(x, y, -p); }
 
+// Post-collision deviations dp_a = N'_a - w_a n_ref at a given Phi:
+//   N'_a = N_a + Omega_a + deltaN_a, Omega_a = -(N_a - J f^eq_a)/tau (Eqs. 12, 20),
+//   N_a - J f^eq_a = (d_a - w_a mdev) - w_a m x_a,
+// with the non-equilibrium part formed first, so that its rounding error is
+// relative to itself and not to the much larger d_a.
+template <int Q, typename R>
+__device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ rc, R m, R mdev,
+                                        R rho, R itau, const R (&U)[Lat<Q>::D],
+                                        const R (&Phi)[Lat<Q>::D], R (&dp)[Q]) {
+  using L = CoefLayout<Q>;
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  R gd[L::NS], dU[D];
+#pragma unroll
+  for (int i = 0; i < L::NS; i++) gd[i] = rc[L::GINV + i];
+  const R h2m = R(0.5) / m;
+#pragma unroll
+  for (int i = 0; i < D; i++) dU[i] = Phi[i] * h2m;
+  EqParts<Q, R> e;
+  eq_parts<Q, R>(gd, U, dU, e);
+  R xe[H + 1], xo[H + 1];
+  xe[0] = eq_even_dev<Q, R>(e, 0);
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    xe[p] = eq_even_dev<Q, R>(e, p);
+    xo[p] = eq_odd<Q, R>(e, U, p);
+  }
+  // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a - L^j_a) f^eq_a   (Eq. 30):
+  // K_a - L_a = K_a + K_abar = M_p, and a pair contributes c_p (f_p - f_pbar)
+  // with f_p - f_pbar = 2 rho w_p xo_p
+  const R cpr = -(R(1) - R(0.5) * itau) * rho;
+  R dP[D][D];
+#pragma unroll
+  for (int i = 0; i < D; i++)
+#pragma unroll
+    for (int j = 0; j < D; j++) dP[i][j] = R(0);
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    const R df = cpr * lat_w<Q, R>(p) * xo[p];
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      const R t = rc[L::MP + (p - 1) * D + j] * df;
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        const int ci = Lat<Q>::c(p, i);
+        if (ci > 0) dP[i][j] += t;
+        if (ci < 0) dP[i][j] -= t;
+      }
+    }
+  }
+  R tr = R(0);
+#pragma unroll
+  for (int i = 0; i < D; i++) tr += dP[i][i];
+  const R J = rc[L::J];
+  {
+    const R w = lat_w<Q, R>(0);
+    const R neq = (d[0] - w * mdev) - (w * m) * xe[0];
+    dp[0] = d[0] - itau * neq - (R(3) * w * J) * tr;
+  }
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    R cF = R(0), cPc = R(0);
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const int ci = Lat<Q>::c(p, i);
+      if (ci == 0) continue;
+      cF += ci > 0 ? Phi[i] : -Phi[i];
+#pragma unroll
+      for (int j = 0; j < D; j++) {
+        const int cj = Lat<Q>::c(p, j);
+        if (cj == 0) continue;
+        cPc += ci * cj > 0 ? dP[i][j] : -dP[i][j];
+      }
+    }
+    const R w = lat_w<Q, R>(p);
+    const R Ep = (R(9) * w * J) * cPc - (R(3) * w * J) * tr;
+    const R Op = (R(3) * w) * cF;
+    const R wd = w * mdev, wm = w * m;
+    const R neqp = (d[p] - wd) - wm * (xe[p] + xo[p]);
+    const R neqm = (d[p + H] - wd) - wm * (xe[p] - xo[p]);
+    dp[p] = d[p] - itau * neqp + (Ep + Op);
+    dp[p + H] = d[p + H] - itau * neqm + (Ep - Op);
+  }
+}
+
 // Full local collision: solve Phi = J G(Phi / J) by a chord iteration
-//   Phi <- Phi + H (J G - Phi),  H = (I - L)^-1,
-// where L is the part of dG/dF that depends only on the cell geometry (it
-// comes from the g^ij U~ terms of Eq. 33 and the c.F term of Eq. 31; the
-// remainder is of order |U| Theta, so each chord step shrinks the error by
-// about that factor). With CHORD = false, H = I (plain fixed-point iteration)
-// and the start value is Phi = 0; with CHORD, the start value is m times the
-// rest-state force. A correction is accepted as converged when it is at most
-// max(tol max(m, |Phi|), 64 eps |Phi|): eps is the unit roundoff of R, and
-// Phi is a sum of some forty rounded terms of its own size, so smaller
-// corrections are rounding noise.
-// With FINAL every evaluation also forms N'. When the correction of an
-// evaluation is accepted, N' is moved by that correction to first order
-// (extrapolate), so the returned N' belongs to the corrected Phi and no
-// further evaluation is needed: a cell whose start value is already within
-// the tolerance costs a single evaluation.
+//   Phi <- Phi + H (Phi_new - Phi),  H = (I - L)^-1,
+// where L is the part of the Jacobian of the map that does not vanish with
+// U (the remainder is of order |U~| times the coefficients, so each chord
+// step shrinks the error by about that factor). With CHORD = false, H = I
+// (plain fixed-point iteration) and the start value is Phi = 0; with CHORD,
+// the start value is m times the rest-state force. A correction is accepted
+// as converged when it is at most max(tol max(m, |Phi|), 64 eps |Phi|): eps
+// is the unit roundoff of R, and Phi is a sum of dozens of rounded terms of
+// its own size, so smaller corrections are rounding noise. With FINAL, the
+// post-collision deviations are formed at the converged Phi.
+// rc points at the cell's coefficient record (global or local memory).
 template <int Q, typename R, bool CHORD, bool FINAL>
-__device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, R> &k, R nref,
+__device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restrict__ rc, R nref,
                                              R tau, R tol, int max_iter, R (&dp)[Q],
                                              CollideState<Q, R> &st) {
-  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  using L = CoefLayout<Q>;
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H, NS = L::NS;
   const R epsn = sizeof(R) == 4 ? R(64.0 / 16777216.0) : R(64.0 / 9007199254740992.0);
   // pair sums s_p = d_p + d_pbar and differences t_p = d_p - d_pbar
   R sp[H + 1], tp[H + 1];
@@ -298,13 +299,12 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
     tp[p] = d[p] - d[p + H];
     mdev += sp[p];
   }
-  CollideConst<Q, R> cc;
-  cc.mdev = mdev;
-  cc.m = nref + mdev;
+  const R m = nref + mdev;
+  const R J = rc[L::J];
   // rho = sum f = sum N / J; rho U = sum c f   (Eqs. 14, 15, 17)
-  st.rho = cc.m / k.J;
-  const R im = R(1) / cc.m;
-  cc.h2m = R(0.5) * im;
+  st.rho = m / J;
+  const R im = R(1) / m;
+  const R h2m = R(0.5) * im;
 #pragma unroll
   for (int i = 0; i < D; i++) {
     R s = R(0);
@@ -316,98 +316,95 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const CellCoef<Q, 
     }
     st.U[i] = s * im;
   }
-  cc.itau = R(1) / tau;
-  // -1/2 (1 - 1/(2 tau)) times the 2 of f_p - f_pbar = 2 rho w xo
-  const R cpi = -(R(1) - R(0.5) * cc.itau);
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    const R w = c == 0 ? lat_w<Q, R>(0) : c == 1 ? lat_w<Q, R>(1) : lat_w<Q, R>(Q == 9 ? 3 : 4);
-    cc.dfw[c] = cpi * st.rho * w;
-    cc.w3J[c] = R(3) * w * k.J;
-    cc.w9J[c] = R(9) * w * k.J;
-    cc.iwm[c] = cc.itau * w * cc.m;
-    cc.wm[c] = w * cc.m;
-    cc.wd[c] = w * mdev;
-  }
+  const R itau = R(1) / tau;
   // constant part of J F: body force m G, 1/2 sum_a L_a N_a (L_a = -K_abar), the
   // reference part -n_ref sum_a w_a K_a of both sums of Eq. 27 (the largest term,
   // the same every step: formed without rounding error from the split KW + KWL),
-  // and the parts of -1/2 sum_a K_a N'_a that do not change during the
-  // iteration. Over a pair,
+  // the parts of -1/2 sum_a K_a N'_a that do not change during the iteration
+  // and the terms of the map that depend on U only. Over a pair,
   //   -1/2 (K_pbar d_p + K_p d_pbar) - 1/2 (1 - 1/tau)(K_p d_p + K_pbar d_pbar)
   //     = -(2 - 1/tau)/4 M_p s_p + (1/tau)/4 D_p t_p.
   R Pb[D];
-  const R am = -R(0.25) * (R(2) - cc.itau), ad = R(0.25) * cc.itau;
+  const R am = -R(0.25) * (R(2) - itau), ad = R(0.25) * itau;
 #pragma unroll
   for (int i = 0; i < D; i++) {
-    const R pr = nref * k.Kw[i];
-    const R err = two_prod_err(nref, k.Kw[i], pr) + nref * k.KwL[i];
-    R s = cc.m * k.G[i] - err - R(0.5) * cc.itau * mdev * k.Kw[i];
+    const R kw = rc[L::KW + i];
+    const R pr = nref * kw;
+    const R err = two_prod_err(nref, kw, pr) + nref * rc[L::KWL + i];
+    R s = m * rc[L::BODY + i] - err - R(0.5) * itau * mdev * kw;
 #pragma unroll
-    for (int p = 1; p <= H; p++) s += am * k.M[p][i] * sp[p] + ad * k.Dk[p][i] * tp[p];
-    Pb[i] = s - pr;
+    for (int p = 1; p <= H; p++)
+      s += am * rc[L::MP + (p - 1) * D + i] * sp[p] + ad * rc[L::DK + (p - 1) * D + i] * tp[p];
+    R u = rc[L::CE + i];
+#pragma unroll
+    for (int l = 0; l < D; l++) u += rc[L::PO1 + i * D + l] * st.U[l];
+    Pb[i] = (s - R(0.5) * m * u) - pr;
   }
-  R Phi[D], Pn[D];
+  R Phi[D];
 #pragma unroll
-  for (int i = 0; i < D; i++) Phi[i] = CHORD ? cc.m * k.Fr[i] : R(0);
+  for (int i = 0; i < D; i++) Phi[i] = CHORD ? m * rc[L::FR + i] : R(0);
   st.conv = false;
   int it = 0;
-  // correction dF = H (Phi_new - Phi); converged when it is at most
-  // max(tol max(m, |Phi|), 64 eps |Phi|)
-  auto correction = [&](R(&dF)[D]) -> bool {
+  while (it < max_iter) {
+    // Phi_new = Pb' - 1/2 { m [PE : U~U~ + PO2 : (U~^k)^2 U~^l + LO U~] + TL Phi }
+    R Ut[D], Ut2[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      Ut[i] = st.U[i] + Phi[i] * h2m;
+      Ut2[i] = Ut[i] * Ut[i];
+    }
+    R UU[NS];
+#pragma unroll
+    for (int k = 0; k < D; k++)
+#pragma unroll
+      for (int l = k; l < D; l++) UU[sym<D>(k, l)] = Ut[k] * Ut[l];
     R r[D];
 #pragma unroll
-    for (int i = 0; i < D; i++) r[i] = Pn[i] - Phi[i];
+    for (int i = 0; i < D; i++) {
+      R a = R(0);
+#pragma unroll
+      for (int s = 0; s < NS; s++) a += rc[L::PE + i * NS + s] * UU[s];
+#pragma unroll
+      for (int k = 0; k < D; k++)
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+          if (k == l) continue;
+          a += rc[L::PO2 + i * L::NO + offd<D>(k, l)] * (Ut2[k] * Ut[l]);
+        }
+#pragma unroll
+      for (int j = 0; j < D; j++) a += rc[L::LO + i * D + j] * Ut[j];
+      R b = R(0);
+#pragma unroll
+      for (int j = 0; j < D; j++) b += rc[L::TL + i * D + j] * Phi[j];
+      r[i] = (Pb[i] - R(0.5) * (m * a + b)) - Phi[i];
+    }
+    it++;
+    // correction dF = H (Phi_new - Phi); converged when it is at most
+    // max(tol max(m, |Phi|), 64 eps |Phi|)
     R diff = R(0), pmax = R(0);
+    R dF[D];
 #pragma unroll
     for (int i = 0; i < D; i++) {
       R x = r[i];
       if (CHORD) {
         x = R(0);
 #pragma unroll
-        for (int j = 0; j < D; j++) x += k.Hm[i][j] * r[j];
+        for (int j = 0; j < D; j++) x += rc[L::HM + i * D + j] * r[j];
       }
       dF[i] = x;
       diff = maxnan(diff, absr(x));
       pmax = maxnan(pmax, absr(Phi[i]));
     }
-    return diff <= maxnan(tol * maxnan(cc.m, pmax), epsn * pmax);
-  };
-  if (!FINAL) {
-    // F only: iteration on Phi_new
-    while (it < max_iter) {
-      eval_phi<Q, R>(k, cc, st.U, Phi, Pb, Pn);
-      it++;
-      R dF[D];
-      const bool ok = correction(dF);
 #pragma unroll
-      for (int i = 0; i < D; i++) Phi[i] += dF[i];
-      if (ok) {
-        st.conv = true;
-        break;
-      }
-    }
-  } else {
-    // every evaluation also forms N'; the accepted correction is applied to
-    // N' by extrapolation
-    while (it < max_iter) {
-      eval_np<Q, R>(d, k, cc, st.U, Phi, Pb, dp, Pn);
-      it++;
-      R dF[D];
-      const bool ok = correction(dF);
-      if (ok) {
-        extrapolate<Q, R>(k, st.U, Phi, cc.h2m, dF, cc.itau, dp);
-#pragma unroll
-        for (int i = 0; i < D; i++) Phi[i] += dF[i];
-        st.conv = true;
-        break;
-      }
-#pragma unroll
-      for (int i = 0; i < D; i++) Phi[i] += dF[i];
+    for (int i = 0; i < D; i++) Phi[i] += dF[i];
+    if (diff <= maxnan(tol * maxnan(m, pmax), epsn * pmax)) {
+      st.conv = true;
+      break;
     }
   }
   st.iters = it;
-  const R iJ = R(1) / k.J;
+  if (FINAL) form_np<Q, R>(d, rc, m, mdev, st.rho, itau, st.U, Phi, dp);
+  const R iJ = R(1) / J;
 #pragma unroll
   for (int i = 0; i < D; i++) st.F[i] = Phi[i] * iJ;
 }

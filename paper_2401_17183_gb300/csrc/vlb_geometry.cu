@@ -312,78 +312,6 @@ struct PackArgs {
   double wall_omega[3][2][3];
 };
 
-// Geometric part L of the Jacobian dG/dF of the fixed-point map of Eq. 27
-// (the terms that do not vanish with U): with
-//   h^l_a = 9/4 [(c.g.c) c^l - T0 (2 (g c)^l + tr(g) c^l)]      (d x_a / dF^l = h^l_a / rho)
-//   P^{ijl} = 2 cpi sum_p w_p c^i_p (K^j_p + K^j_pbar) h^l_p  (d deltaPi^ij / dF^l)
-//   L^{il} = -1/2 sum_a w_a K^i_a [h^l_a / tau + 3 c^l_a + 3 (3 c_a.P^l.c_a - tr P^l)]
-// returns H = (I - L)^-1.
-template <int Q>
-__device__ void chord_matrix(const CellCoef<Q, double> &k, const double (&K)[Q][Lat<Q>::D], double tau,
-                             double (&Hm)[Lat<Q>::D][Lat<Q>::D]) {
-  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  const double T0 = kT0, itau = 1.0 / tau, cpi = -0.5 * (1.0 - 0.5 * itau);
-  double g[D][D], trg = 0.0;
-  for (int i = 0; i < D; i++)
-    for (int j = 0; j < D; j++) g[i][j] = k.gd[sym<D>(i, j)] + (i == j ? 1.0 : 0.0);
-  for (int i = 0; i < D; i++) trg += g[i][i];
-  double h[Q][D];
-  for (int a = 0; a < Q; a++) {
-    double c[D], gc[D], cgc = 0.0;
-    for (int i = 0; i < D; i++) c[i] = Lat<Q>::c(a, i);
-    for (int i = 0; i < D; i++) {
-      gc[i] = 0.0;
-      for (int j = 0; j < D; j++) gc[i] += g[i][j] * c[j];
-      cgc += c[i] * gc[i];
-    }
-    for (int l = 0; l < D; l++) h[a][l] = 2.25 * (cgc * c[l] - T0 * (2.0 * gc[l] + trg * c[l]));
-  }
-  double L[D][D];
-  for (int l = 0; l < D; l++) {
-    double P[D][D];
-    for (int i = 0; i < D; i++)
-      for (int j = 0; j < D; j++) {
-        double s = 0.0;
-        for (int p = 1; p <= H; p++)
-          s += lat_w<Q, double>(p) * Lat<Q>::c(p, i) * (K[p][j] + K[p + H][j]) * h[p][l];
-        P[i][j] = 2.0 * cpi * s;
-      }
-    double trP = 0.0;
-    for (int i = 0; i < D; i++) trP += P[i][i];
-    for (int i = 0; i < D; i++) {
-      double s = 0.0;
-      for (int a = 1; a < Q; a++) {
-        double cPc = 0.0;
-        for (int x = 0; x < D; x++)
-          for (int y = 0; y < D; y++) cPc += Lat<Q>::c(a, x) * Lat<Q>::c(a, y) * P[x][y];
-        s += lat_w<Q, double>(a) * K[a][i] *
-             (h[a][l] * itau + 3.0 * Lat<Q>::c(a, l) + 3.0 * (3.0 * cPc - trP));
-      }
-      L[i][l] = -0.5 * s;
-    }
-  }
-  double A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-  for (int i = 0; i < D; i++)
-    for (int j = 0; j < D; j++) A[i][j] = (i == j ? 1.0 : 0.0) - L[i][j];
-  if (D == 2) {
-    const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-    Hm[0][0] = A[1][1] / det;
-    Hm[0][1] = -A[0][1] / det;
-    Hm[1][0] = -A[1][0] / det;
-    Hm[1][1] = A[0][0] / det;
-  } else {
-    double C[3][3];
-    for (int i = 0; i < 3; i++)
-      for (int j = 0; j < 3; j++) {
-        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-        C[j][i] = A[i1][j1] * A[i2][j2] - A[i1][j2] * A[i2][j1];  // adjugate (transposed cofactors)
-      }
-    const double det = A[0][0] * C[0][0] + A[0][1] * C[1][0] + A[0][2] * C[2][0];
-    for (int i = 0; i < D; i++)
-      for (int j = 0; j < D; j++) Hm[i][j] = C[i][j] / det;
-  }
-}
-
 template <int Q, typename R>
 __global__ void k_pack_coef(const PackArgs a, R *coef) {
   constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
@@ -392,69 +320,37 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.nrec) return;
   const int64_t c = a.plane ? r * a.nfast : r;
-  R *out = coef + r * RS;
-  for (int k = 0; k < RS; k++) out[k] = R(0);
-  out[L::J] = static_cast<R>(a.J[c]);
-  for (int i = 0; i < D; i++)
-    for (int j = i; j < D; j++)
-      out[L::GINV + sym<D>(i, j)] = static_cast<R>(a.ginv[c * NS + sym<D>(i, j)] - (i == j ? 1.0 : 0.0));
+  double K[Q][D], G[D], rec[L::NC];
+  for (int av = 0; av < Q; av++)
+    for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
   for (int i = 0; i < D; i++) {
     double s = 0.0;
     for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];  // G^i = G . g^i
-    out[L::BODY + i] = static_cast<R>(s);
+    G[i] = s;
   }
-  double K[Q][D];
-  for (int av = 0; av < Q; av++)
-    for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
-  // pair sums and differences of the link coefficients, formed in FP64
-  for (int p = 1; p <= H; p++)
-    for (int i = 0; i < D; i++) {
-      out[L::MP + (p - 1) * D + i] = static_cast<R>(K[p][i] + K[p + H][i]);
-      out[L::DK + (p - 1) * D + i] = static_cast<R>(K[p][i] - K[p + H][i]);
-    }
-  // reference-state part of J F: sum_a w_a K^i_a, as a hi/lo pair
-  for (int i = 0; i < D; i++) {
-    double s = 0.0;
-    for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * K[av][i];
-    const R hi = static_cast<R>(s);
-    out[L::KW + i] = hi;
-    out[L::KWL + i] = static_cast<R>(s - static_cast<double>(hi));
-  }
-  // chord matrix and rest-state force
+  build_record<Q>(a.J[c], a.ginv + c * NS, G, K, a.tau, rec);
+  // F at rest (rho = 1, U = 0), the start value of the chord iteration
   {
-    CellCoef<Q, double> k;
-    k.J = a.J[c];
-    for (int i = 0; i < NS; i++) k.gd[i] = a.ginv[c * NS + i];
-    for (int i = 0; i < D; i++) k.gd[sym<D>(i, i)] -= 1.0;
-    for (int i = 0; i < D; i++) {
-      double s = 0.0;
-      for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
-      k.G[i] = s;
-      k.KwL[i] = 0.0;
-      k.Fr[i] = 0.0;
-      double w = 0.0;
-      for (int av = 1; av < Q; av++) w += lat_w<Q, double>(av) * K[av][i];
-      k.Kw[i] = w;
-      for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
-    }
-    pairs_from_K<Q, double>(K, k);
-    double Hm[D][D];
-    chord_matrix<Q>(k, K, a.tau, Hm);
-    for (int i = 0; i < D; i++)
-      for (int j = 0; j < D; j++) out[L::HM + i * D + j] = static_cast<R>(Hm[i][j]);
-    // F at rest (rho = 1, U = 0), the start value of the chord iteration
-    double N[Q], U0[D];
+    double gd[NS], U0[D], N[Q], Np[Q];
+    for (int i = 0; i < NS; i++) gd[i] = rec[L::GINV + i];
     for (int i = 0; i < D; i++) U0[i] = 0.0;
     EqParts<Q, double> e;
-    eq_parts<Q, double>(k.gd, U0, U0, e);
+    eq_parts<Q, double>(gd, U0, U0, e);
     for (int av = 0; av < Q; av++) {
       const int p = av <= H ? av : av - H;
-      N[av] = k.J * lat_w<Q, double>(av) * eq_even<Q, double>(e, p);
+      N[av] = rec[L::J] * lat_w<Q, double>(av) * eq_even<Q, double>(e, p);
     }
-    double Np[Q];
     CollideState<Q, double> cs;
-    collide_cell<Q, double, false, false>(N, k, 0.0, a.tau, 1e-15, 400, Np, cs);
-    for (int i = 0; i < D; i++) out[L::FR + i] = static_cast<R>(cs.conv ? cs.F[i] : 0.0);
+    collide_cell<Q, double, false, false>(N, rec, 0.0, a.tau, 1e-15, 400, Np, cs);
+    for (int i = 0; i < D; i++) rec[L::FR + i] = cs.conv ? cs.F[i] : 0.0;
+  }
+  R *out = coef + r * RS;
+  for (int k = 0; k < RS; k++) out[k] = k < L::NC ? static_cast<R>(rec[k]) : R(0);
+  // reference-state part of J F as a hi/lo pair
+  for (int i = 0; i < D; i++) {
+    const R hi = static_cast<R>(rec[L::KW + i]);
+    out[L::KW + i] = hi;
+    out[L::KWL + i] = static_cast<R>(rec[L::KW + i] - static_cast<double>(hi));
   }
   // wall velocity: rigid motion of the adjacent wall, at the point halfway to the ghost node
   const Addr<Q> ad(a.g, c);

@@ -70,60 +70,53 @@ __host__ __device__ constexpr int sym(int i, int j) {
   return D == 2 ? i + j : (i < j ? i : j) == 0 ? (i > j ? i : j) : (i < j ? i : j) == 1 ? 2 + (i > j ? i : j) : 5;
 }
 
+// index of the ordered off-diagonal pair (k, l), k != l, in a D(D-1) array
+template <int D>
+__host__ __device__ constexpr int offd(int k, int l) {
+  return k * (D - 1) + (l < k ? l : l - 1);
+}
+
 // --------------------------------------------------------------------------
 // Coefficient record of one cell (or one column in plane mode). Records are
 // stored one after another (record r at coef + r * RS) and padded to a
-// multiple of 16 bytes, so a thread reads its record with 16-byte vector
-// loads from one base address. Link coefficients are stored per pair
-// (p, pbar = p + H) as M_p = K_p + K_pbar and D_p = K_p - K_pbar.
+// multiple of 16 bytes. Everything in a record is a function of the cell
+// geometry and tau alone, formed once in FP64 and rounded to the storage type.
+//
+// Link coefficients are stored per pair (p, pbar = p + H) as
+// M_p = K_p + K_pbar and D_p = K_p - K_pbar. The remaining blocks are the
+// coefficients of the fixed-point map of Eq. 27 written as a polynomial in
+// U~ (see build_record), so that one evaluation of the map costs a few dozen
+// products instead of a pass over all directions.
 template <int Q>
 struct CoefLayout {
   static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  static constexpr int NS = D * (D + 1) / 2;
+  static constexpr int NS = D * (D + 1) / 2;   // symmetric pairs
+  static constexpr int NO = D * (D - 1);       // ordered off-diagonal pairs
+  // set-up of a collision
   static constexpr int J = 0;                  // J (Eq. 5)
   static constexpr int GINV = 1;               // g^ij - delta^ij packed (Eq. 8)
   static constexpr int BODY = GINV + NS;       // G^i = G . g^i
   static constexpr int KW = BODY + D;          // sum_a w_a K^i_a (reference-state part of J F)
   static constexpr int KWL = KW + D;           // its low part: KW + KWL = the FP64 value
-  static constexpr int HM = KWL + D;           // chord matrix (I - L)^-1, row-major D x D
-  static constexpr int FR = HM + D * D;        // F of the rest state at rho = 1 (start value)
+  static constexpr int FR = KWL + D;           // F of the rest state at rho = 1 (start value)
   static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
-  static constexpr int MP = UW + D;            // M_p^i, p = 1..H: MP + (p-1)*D + i
+  static constexpr int CE = UW + D;            // constant term of the map
+  static constexpr int PO1 = CE + D;           // D x D: coefficient of U
+  static constexpr int MP = PO1 + D * D;       // M_p^i, p = 1..H: MP + (p-1)*D + i
   static constexpr int DK = MP + H * D;        // D_p^i
-  static constexpr int NC = DK + H * D;
+  // one evaluation of the map
+  static constexpr int HM = DK + H * D;        // D x D chord matrix (I - L)^-1
+  static constexpr int PE = HM + D * D;        // D x NS: coefficient of U~^k U~^l (k <= l)
+  static constexpr int PO2 = PE + D * NS;      // D x NO: coefficient of (U~^k)^2 U~^l (k != l)
+  static constexpr int LO = PO2 + D * NO;      // D x D: coefficient of U~
+  static constexpr int TL = LO + D * D;        // D x D: coefficient of J F
+  static constexpr int NC = TL + D * D;
   // record stride in elements of type R (16-byte multiple)
   template <typename R>
   static constexpr int stride() {
     return (NC + (int)(16 / sizeof(R)) - 1) / (int)(16 / sizeof(R)) * (int)(16 / sizeof(R));
   }
 };
-
-// Per-cell coefficients held in registers during a collision.
-template <int Q, typename R>
-struct CellCoef {
-  static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  R J;
-  R gd[D * (D + 1) / 2];  // g^ij - delta^ij: stored as a deviation so that rounding is
-                          // relative to the (small) departure from a uniform lattice
-  R G[D];
-  R Kw[D], KwL[D];
-  R Hm[D][D];
-  R Fr[D];
-  R M[H + 1][D];   // K_p + K_pbar (index 0 unused, zero)
-  R Dk[H + 1][D];  // K_p - K_pbar
-};
-
-// pair sums and differences from per-direction link coefficients K[a][i]
-template <int Q, typename R, typename KT>
-__host__ __device__ __forceinline__ void pairs_from_K(const KT &K, CellCoef<Q, R> &k) {
-  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
-  for (int i = 0; i < D; i++) k.M[0][i] = k.Dk[0][i] = R(0);
-  for (int p = 1; p <= H; p++)
-    for (int i = 0; i < D; i++) {
-      k.M[p][i] = R(K[p][i] + K[p + H][i]);
-      k.Dk[p][i] = R(K[p][i] - K[p + H][i]);
-    }
-}
 
 constexpr double kT0 = 1.0 / 3.0;
 
@@ -140,19 +133,19 @@ __device__ __forceinline__ double absr(double x) { return fabs(x); }
 // components are in {-1, 0, 1}. With
 //   B^ij  = (g^ij - delta^ij) T0 + U~^i U~^j,
 //   C^ijk = T0 [(g^ij U~^k - delta^ij U^k) + cyclic] + U~^i U~^j U~^k,
-//   v^i   = sum_j C^ijj,
 // the bracket of Eq. 33 is
-//   1 + c.U/T0 + (c.B.c/T0 - tr B)/(2 T0) + (C[c,c,c] - 3 T0 c.v)/(6 T0^3),
-// and C[c,c,c] only needs C^iii and C^iij for velocities with at most two
-// non-zero components. The struct holds the direction-independent parts.
+//   1 + c.U/T0 + (c.B.c/T0 - tr B)/(2 T0) + (C[c,c,c] - 3 T0 c^i C^ijj)/(6 T0^3).
+// On such sets (c^k)^3 = c^k, and the last term reduces to
+//   (9/2) sum_{k != l} C^kkl c^l (3 (c^k)^2 - 1):
+// the C^kkk terms of C[c,c,c] and of c^i C^ijj cancel, and C^123 never meets
+// a velocity with three non-zero components on D3Q19. So only C^kkl (k != l)
+// is formed. The struct holds the direction-independent parts.
 template <int Q, typename R>
 struct EqParts {
   static constexpr int D = Lat<Q>::D;
   R B[D][D];
   R trB;
-  R C3[D];      // C^iii
-  R C2[D][D];   // C2[i][j] = C^iij, i != j
-  R v[D];       // v^i = sum_j C^ijj
+  R C2[D][D];   // C2[k][l] = C^kkl, k != l
 };
 
 template <int Q, typename R>
@@ -175,8 +168,6 @@ __device__ __forceinline__ void eq_parts(const R (&gd)[Lat<Q>::D * (Lat<Q>::D + 
   for (int i = 0; i < D; i++) e.trB += e.B[i][i];
 #pragma unroll
   for (int i = 0; i < D; i++) {
-    // C^iii = 3 T0 (g^ii U~^i - U^i) + (U~^i)^3, 3 T0 = 1
-    e.C3[i] = (gd[sym<D>(i, i)] * Ut[i] + dU[i]) + Ut[i] * Ut[i] * Ut[i];
 #pragma unroll
     for (int j = 0; j < D; j++) {
       if (i == j) continue;
@@ -184,14 +175,6 @@ __device__ __forceinline__ void eq_parts(const R (&gd)[Lat<Q>::D * (Lat<Q>::D + 
       e.C2[i][j] = T0 * ((gd[sym<D>(i, i)] * Ut[j] + dU[j]) + R(2) * gd[sym<D>(i, j)] * Ut[i]) +
                    Ut[i] * Ut[i] * Ut[j];
     }
-  }
-#pragma unroll
-  for (int i = 0; i < D; i++) {
-    R s = e.C3[i];
-#pragma unroll
-    for (int j = 0; j < D; j++)
-      if (j != i) s += e.C2[j][i];  // C^ijj = C^jji
-    e.v[i] = s;
   }
 }
 
@@ -242,37 +225,26 @@ __device__ __forceinline__ R eq_even_dev(const EqParts<Q, R> &e, int a) {
   return (R(3) * cbc - e.trB) * R(1.5);  // (c.B.c / T0 - tr B) / (2 T0)
 }
 
-// odd part of the bracket of Eq. 33 for direction a
+// odd part of the bracket of Eq. 33 for direction a:
+//   c.U / T0 + (9/2) sum_{k != l} C^kkl c^l (3 (c^k)^2 - 1)
 template <int Q, typename R>
 __device__ __forceinline__ R eq_odd(const EqParts<Q, R> &e, const R (&U)[Lat<Q>::D], int a) {
   constexpr int D = Lat<Q>::D;
-  R cu = R(0), cv = R(0), ccc = R(0);
+  R cu = R(0), cc = R(0);
 #pragma unroll
-  for (int i = 0; i < D; i++) {
-    const int ci = Lat<Q>::c(a, i);
-    if (ci == 0) continue;
-    if (ci > 0) {
-      cu += U[i];
-      cv += e.v[i];
-      ccc += e.C3[i];
-    } else {
-      cu -= U[i];
-      cv -= e.v[i];
-      ccc -= e.C3[i];
-    }
+  for (int l = 0; l < D; l++) {
+    const int cl = Lat<Q>::c(a, l);
+    if (cl == 0) continue;
+    cu += cl > 0 ? U[l] : -U[l];
 #pragma unroll
-    for (int j = 0; j < D; j++) {
-      const int cj = Lat<Q>::c(a, j);
-      // orderings (i,i,j), (i,j,i), (j,i,i): 3 c_i c_i c_j C^iij = 3 c_j C^iij
-      if (j == i || cj == 0) continue;
-      if (cj > 0)
-        ccc += R(3) * e.C2[i][j];
-      else
-        ccc -= R(3) * e.C2[i][j];
+    for (int k = 0; k < D; k++) {
+      if (k == l) continue;
+      // 3 (c^k)^2 - 1 is 2 for an in-plane k and -1 otherwise
+      const int f = Lat<Q>::c(a, k) != 0 ? 2 : -1;
+      cc += R(f * cl) * e.C2[k][l];
     }
   }
-  // c.U / T0 + (C[c,c,c] - 3 T0 c.v) / (6 T0^3), with 3 T0 = 1 and 1/(6 T0^3) = 9/2
-  return R(3) * cu + R(4.5) * (ccc - cv);
+  return R(3) * cu + R(4.5) * cc;
 }
 
 // --------------------------------------------------------------------------

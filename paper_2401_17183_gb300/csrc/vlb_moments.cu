@@ -61,31 +61,19 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
     pull<Q, ODD, S, double>(f, a.ncell, ad, N);
 #pragma unroll
     for (int av = 0; av < Q; av++) N[av] += lat_w<Q, double>(av) * a.nref;
-    CellCoef<Q, double> k;
-    k.J = a.J[c];
-    for (int i = 0; i < NS; i++) k.gd[i] = a.ginv[c * NS + i];
-    for (int i = 0; i < D; i++) k.gd[sym<D>(i, i)] -= 1.0;
+    double K[Q][D], G[D], rec[CoefLayout<Q>::NC];
+    for (int av = 0; av < Q; av++)
+      for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
     for (int i = 0; i < D; i++) {
       double s = 0.0;
       for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
-      k.G[i] = s;
-      k.KwL[i] = 0.0;
-      k.Fr[i] = 0.0;
-      for (int j = 0; j < D; j++) k.Hm[i][j] = 0.0;
+      G[i] = s;
     }
-    double K[Q][D];
-    for (int av = 0; av < Q; av++)
-      for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
-    pairs_from_K<Q, double>(K, k);
-    for (int i = 0; i < D; i++) {
-      double s = 0.0;
-      for (int av = 1; av < Q; av++) s += lat_w<Q, double>(av) * K[av][i];
-      k.Kw[i] = s;  // sum_a w_a K_a
-    }
+    build_record<Q>(a.J[c], a.ginv + c * NS, G, K, a.tau, rec);
     double Np[Q];
     CollideState<Q, double> st;
     // plain fixed point from F = 0 on the full populations (n_ref = 0)
-    collide_cell<Q, double, false, false>(N, k, 0.0, a.tau, 1e-14, 200, Np, st);
+    collide_cell<Q, double, false, false>(N, rec, 0.0, a.tau, 1e-14, 200, Np, st);
     if (!st.conv) atomicOr(a.err, ERR_NOCONV);
     double gl[D][D];
     for (int i = 0; i < D; i++)
