@@ -113,8 +113,8 @@ __device__ void build_record(double J, const double *ginv, const double *G,
       M[p][i] = K[p][i] + K[p + H][i];
       Dk[p][i] = K[p][i] - K[p + H][i];
       c[p][i] = Lat<Q>::c(p, i);
-      rec[L::MP + (p - 1) * D + i] = M[p][i];
-      rec[L::DK + (p - 1) * D + i] = Dk[p][i];
+      rec[L::mp(p, i)] = M[p][i];
+      rec[L::dk(p, i)] = Dk[p][i];
     }
   }
   double Rt[D][D][D];
@@ -227,7 +227,7 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
     const R df = cpr * lat_w<Q, R>(p) * xo[p];
 #pragma unroll
     for (int j = 0; j < D; j++) {
-      const R t = rc[L::MP + (p - 1) * D + j] * df;
+      const R t = rc[L::mp(p, j)] * df;
 #pragma unroll
       for (int i = 0; i < D; i++) {
         const int ci = Lat<Q>::c(p, i);
@@ -334,7 +334,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     R s = m * rc[L::BODY + i] - err - R(0.5) * itau * mdev * kw;
 #pragma unroll
     for (int p = 1; p <= H; p++)
-      s += am * rc[L::MP + (p - 1) * D + i] * sp[p] + ad * rc[L::DK + (p - 1) * D + i] * tp[p];
+      s += am * rc[L::mp(p, i)] * sp[p] + ad * rc[L::dk(p, i)] * tp[p];
     R u = rc[L::CE + i];
 #pragma unroll
     for (int l = 0; l < D; l++) u += rc[L::PO1 + i * D + l] * st.U[l];

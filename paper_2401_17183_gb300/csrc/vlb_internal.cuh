@@ -78,15 +78,20 @@ __host__ __device__ constexpr int offd(int k, int l) {
 
 // --------------------------------------------------------------------------
 // Coefficient record of one cell (or one column in plane mode). Records are
-// stored one after another (record r at coef + r * RS) and padded to a
-// multiple of 16 bytes. Everything in a record is a function of the cell
-// geometry and tau alone, formed once in FP64 and rounded to the storage type.
+// stored one after another (record r at coef + r * RS). Everything in a
+// record is a function of the cell geometry and tau alone, formed once in
+// FP64 and rounded to the storage type. The record falls into three groups,
+// each starting on a multiple of four elements (16 bytes or more), so that a
+// group can be read with vector loads: the set-up of a collision, the link
+// coefficients, and the coefficients of one evaluation of the map.
 //
 // Link coefficients are stored per pair (p, pbar = p + H) as
-// M_p = K_p + K_pbar and D_p = K_p - K_pbar. The remaining blocks are the
-// coefficients of the fixed-point map of Eq. 27 written as a polynomial in
-// U~ (see build_record), so that one evaluation of the map costs a few dozen
-// products instead of a pass over all directions.
+// M_p = K_p + K_pbar and D_p = K_p - K_pbar, interleaved pair by pair. The
+// last group holds the coefficients of the fixed-point map of Eq. 27 written
+// as a polynomial in U~ (see build_record), so that one evaluation of the map
+// costs a few dozen products instead of a pass over all directions.
+__host__ __device__ constexpr int round4(int n) { return (n + 3) / 4 * 4; }
+
 template <int Q>
 struct CoefLayout {
   static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
@@ -102,19 +107,22 @@ struct CoefLayout {
   static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
   static constexpr int CE = UW + D;            // constant term of the map
   static constexpr int PO1 = CE + D;           // D x D: coefficient of U
-  static constexpr int MP = PO1 + D * D;       // M_p^i, p = 1..H: MP + (p-1)*D + i
-  static constexpr int DK = MP + H * D;        // D_p^i
+  // link coefficients: M_p^i at MPD + (p-1)*2D + i, D_p^i at MPD + (p-1)*2D + D + i
+  static constexpr int MPD = round4(PO1 + D * D);
   // one evaluation of the map
-  static constexpr int HM = DK + H * D;        // D x D chord matrix (I - L)^-1
+  static constexpr int HM = round4(MPD + 2 * H * D);  // D x D chord matrix (I - L)^-1
   static constexpr int PE = HM + D * D;        // D x NS: coefficient of U~^k U~^l (k <= l)
   static constexpr int PO2 = PE + D * NS;      // D x NO: coefficient of (U~^k)^2 U~^l (k != l)
   static constexpr int LO = PO2 + D * NO;      // D x D: coefficient of U~
   static constexpr int TL = LO + D * D;        // D x D: coefficient of J F
   static constexpr int NC = TL + D * D;
-  // record stride in elements of type R (16-byte multiple)
+  __host__ __device__ static constexpr int mp(int p, int i) { return MPD + (p - 1) * 2 * D + i; }
+  __host__ __device__ static constexpr int dk(int p, int i) { return MPD + (p - 1) * 2 * D + D + i; }
+  // record stride in elements of type R: a multiple of four elements, so that
+  // every record and group starts on a 16-byte boundary
   template <typename R>
   static constexpr int stride() {
-    return (NC + (int)(16 / sizeof(R)) - 1) / (int)(16 / sizeof(R)) * (int)(16 / sizeof(R));
+    return round4(NC);
   }
 };
 

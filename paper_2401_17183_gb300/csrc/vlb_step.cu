@@ -25,6 +25,7 @@
 // reading tile k + 1 ahead of the writes of tile k is safe.
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "vlb_addr.cuh"
@@ -106,12 +107,27 @@ constexpr int step_min_blocks() {
   return sizeof(R) == 4 ? 4 : 2;
 }
 
-template <int Q, typename S, typename R, bool ODD, typename IT>
+// pipeline depth: tiles whose copies are in flight while one is collided
+constexpr int kStages = 3;
+
+// Shared memory of one block: per stage, the populations of its 128 cells and,
+// in plane mode, the coefficient record they all share.
+template <int Q, typename S, typename R>
+struct StepSmem {
+  static constexpr int RS = CoefLayout<Q>::template stride<R>();
+  alignas(16) R rec[kStages][RS];
+  S pop[kStages][Q][kStepThreads];
+};
+
+template <int Q, typename S, typename R, bool ODD, bool PLANE, typename IT>
 __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(const StepArgs a) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
   constexpr int RS = L::template stride<R>();
-  __shared__ S buf[2][Q][kStepThreads];
+  constexpr int RCHUNK = RS * (int)sizeof(R) / 16;  // 16-byte pieces of a record
+  static_assert(RCHUNK <= kStepThreads, "record larger than one copy per thread");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<Q, S, R> &sm = *reinterpret_cast<StepSmem<Q, S, R> *>(smem_raw);
   const int64_t t0 = (int64_t)blockIdx.x * a.per_block;
   const int64_t t1 = t0 + a.per_block < a.ntiles ? t0 + a.per_block : a.ntiles;
   if (t0 >= t1) return;
@@ -121,29 +137,47 @@ __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(con
   const IT nfast = (IT)(D == 3 ? a.g.n[2] : a.g.n[1]);
   const int tid = threadIdx.x;
 
-  // issue the copies of this thread's cell in tile c into stage st
+  // issue this thread's copies for tile c into stage st: the populations of
+  // its cell and, in plane mode, one 16-byte piece of the shared record
   auto prefetch = [&](const TileCursor &c, int st) {
     const IT ifast = (IT)c.tf * kStepThreads + (IT)tid;
     if (ifast < nfast) {
       const Addr<Q, IT> ad = tile_addr<Q, IT>(a.g, c, ifast);
 #pragma unroll
-      for (int av = 0; av < Q; av++) cp_async<sizeof(S)>(&buf[st][av][tid], f + src_index<Q, ODD, IT>(ps, ad, av));
+      for (int av = 0; av < Q; av++)
+        cp_async<sizeof(S)>(&sm.pop[st][av][tid], f + src_index<Q, ODD, IT>(ps, ad, av));
     }
-    cp_async_commit();
+    if (PLANE && tid < RCHUNK) {
+      const int64_t rec = (int64_t)c.A * a.nB + c.B;
+      cp_async<16>(reinterpret_cast<unsigned char *>(&sm.rec[st][0]) + 16 * tid,
+                   reinterpret_cast<const unsigned char *>(coef + rec * RS) + 16 * tid);
+    }
   };
 
+  // prologue: tiles t0 .. t0 + kStages - 2, one copy group each
   TileCursor cur, nxt;
   cur.set(t0, a);
   nxt = cur;
-  prefetch(cur, 0);
-  for (int64_t t = t0; t < t1; t++) {
-    const int st = (int)((t - t0) & 1);
+#pragma unroll
+  for (int k = 0; k < kStages - 1; k++) {
+    if (t0 + k < t1) prefetch(nxt, k);
+    cp_async_commit();
     nxt.next(a);
-    if (t + 1 < t1)
-      prefetch(nxt, st ^ 1);
-    else
+  }
+  int st = 0;
+  for (int64_t t = t0; t < t1; t++) {
+    // the copies of tile t (this thread's) are complete; after the barrier
+    // every thread's are, and every thread is done with tile t - 1, whose
+    // stage the next prefetch reuses
+    cp_async_wait<kStages - 2>();
+    __syncthreads();
+    {
+      int sn = st + kStages - 1;
+      if (sn >= kStages) sn -= kStages;
+      if (t + kStages - 1 < t1) prefetch(nxt, sn);
       cp_async_commit();
-    cp_async_wait<1>();  // the copies of tile t are complete
+      nxt.next(a);
+    }
 
     const IT ifast = (IT)cur.tf * kStepThreads + (IT)tid;
     if (ifast < nfast) {
@@ -152,12 +186,11 @@ __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(con
       // ---- pull (read side of Eq. 22): deviations d_a = N_a - w_a n_ref
       R N[Q];
 #pragma unroll
-      for (int av = 0; av < Q; av++) N[av] = static_cast<R>(buf[st][av][tid]);
+      for (int av = 0; av < Q; av++) N[av] = static_cast<R>(sm.pop[st][av][tid]);
 
-      // ---- coefficients: one record per column of the fastest axis (plane
-      // mode), the same for every thread of the tile, or one per cell
-      const IT rec = a.plane ? (IT)cur.A * (IT)a.nB + (IT)cur.B : cell;
-      const R *__restrict__ rc = coef + (int64_t)rec * RS;
+      // ---- coefficients: in plane mode one record per column of the fastest
+      // axis, shared by the tile and staged in shared memory; else one per cell
+      const R *__restrict__ rc = PLANE ? &sm.rec[st][0] : coef + (int64_t)cell * RS;
 
       // ---- collide (section 2.2)
       R Np[Q];
@@ -201,14 +234,15 @@ __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(con
       }
       f[cell] = static_cast<S>(Np[0]);
     }
-    cur = nxt;
+    cur.next(a);
+    if (++st == kStages) st = 0;
   }
   cp_async_wait<0>();
 }
 
 // blocks the persistent kernel can keep resident on the current device
 // (queried once per kernel and device)
-static int resident_blocks(const void *kern) {
+static int resident_blocks(const void *kern, size_t smem) {
   static std::mutex mu;
   static std::vector<std::tuple<const void *, int, int>> cache;
   int dev = 0;
@@ -217,7 +251,8 @@ static int resident_blocks(const void *kern) {
   for (const auto &e : cache)
     if (std::get<0>(e) == kern && std::get<1>(e) == dev) return std::get<2>(e);
   int nb = 0, nsm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStepThreads, 0);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStepThreads, smem);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int total = (nb > 0 ? nb : 1) * (nsm > 0 ? nsm : 1);
   cache.emplace_back(kern, dev, total);
@@ -252,23 +287,31 @@ static cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
   // 32-bit indexing when every population offset fits
   const bool i32 = (int64_t)Q * m->ncell < ((int64_t)1 << 31);
   if (a.ntiles == 0) return cudaSuccess;
+  const size_t smem = sizeof(StepSmem<Q, S, R>);
   auto go = [&](void (*kern)(StepArgs)) {
-    const int64_t nblk_max = resident_blocks(reinterpret_cast<const void *>(kern));
+    const int64_t nblk_max = resident_blocks(reinterpret_cast<const void *>(kern), smem);
     a.per_block = (a.ntiles + nblk_max - 1) / nblk_max;
     const int64_t nblk = (a.ntiles + a.per_block - 1) / a.per_block;
-    kern<<<(unsigned)nblk, kStepThreads, 0, s>>>(a);
+    kern<<<(unsigned)nblk, kStepThreads, smem, s>>>(a);
   };
-  if (i32) {
-    if (odd)
-      go(k_step<Q, S, R, true, int32_t>);
-    else
-      go(k_step<Q, S, R, false, int32_t>);
-  } else {
-    if (odd)
-      go(k_step<Q, S, R, true, int64_t>);
-    else
-      go(k_step<Q, S, R, false, int64_t>);
-  }
+  auto pick = [&](auto plane_tag) {
+    constexpr bool P = decltype(plane_tag)::value;
+    if (i32) {
+      if (odd)
+        go(k_step<Q, S, R, true, P, int32_t>);
+      else
+        go(k_step<Q, S, R, false, P, int32_t>);
+    } else {
+      if (odd)
+        go(k_step<Q, S, R, true, P, int64_t>);
+      else
+        go(k_step<Q, S, R, false, P, int64_t>);
+    }
+  };
+  if (a.plane)
+    pick(std::true_type{});
+  else
+    pick(std::false_type{});
   return cudaGetLastError();
 }
 
