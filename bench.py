@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_CELL = {("19", "f32"): 2 * 19 * 4, ("19", "f64"): 2 * 19 * 8, ("9", "f32"): 2 * 9 * 4,
                   ("9", "f64"): 2 * 9 * 8}
-STEP_SOURCES = ["vlb_step.cu", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_internal.cuh"]
+STEP_SOURCES = ["vlb_step.cu", "vlb_step.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_internal.cuh"]
 
 
 def args_parse():

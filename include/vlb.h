@@ -51,7 +51,8 @@ enum vlb_status {
 
 enum vlb_lattice_kind { VLB_D2Q9 = 9, VLB_D3Q19 = 19 };
 enum vlb_bc { VLB_PERIODIC = 0, VLB_WALL = 1 };
-enum vlb_precision { VLB_F64 = 0, VLB_F32 = 1 };
+enum vlb_precision { VLB_F64 = 0, VLB_F32 = 1, VLB_F16 = 2, VLB_BF16 = 3 };
+enum vlb_reference { VLB_REF_UNIFORM = 0, VLB_REF_REST = 1 };
 enum vlb_coef_mode { VLB_COEF_AUTO = 0, VLB_COEF_FULL = 1, VLB_COEF_PLANE = 2 };
 enum vlb_wall_links { VLB_WALL_LINKS_ZERO = 0, VLB_WALL_LINKS_GHOST = 1 };
 
@@ -86,7 +87,20 @@ typedef struct {
  *   tau          BGK relaxation time (Eq. 20), > 1/2
  *   precision    VLB_F64: FP64 populations and arithmetic;
  *                VLB_F32: FP32 populations, FP32 arithmetic, FP32 coefficients
- *                rounded from the FP64 precompute
+ *                rounded from the FP64 precompute;
+ *                VLB_F16 / VLB_BF16: populations stored in 16 bits (IEEE half
+ *                or bfloat16) as deviations from a reference (see reference),
+ *                FP32 arithmetic and coefficients as for VLB_F32. Storage
+ *                rounding is not mass-conserving: each stored deviation is
+ *                rounded to 11 (half) or 8 (bfloat16) significant bits
+ *   reference    what a 16-bit population is stored relative to:
+ *                VLB_REF_UNIFORM: N_a - w_a n_ref with one n_ref for the mesh
+ *                (the scheme FP32/FP64 always use);
+ *                VLB_REF_REST: N_a minus the rest state of Eq. 33 (rho = 1,
+ *                U = 0) on the metric of the storage location's cell, which
+ *                leaves only the flow in the stored value. Needs plane mode
+ *                (the references of a column's neighbours are then
+ *                per-column constants). Ignored for VLB_F32 and VLB_F64
  *   coef_mode    VLB_COEF_FULL streams one coefficient record per cell;
  *                VLB_COEF_PLANE stores one record per column of the fastest
  *                axis and is only accepted when the mesh geometry does not
@@ -99,7 +113,7 @@ typedef struct {
  *                x_wall halfway between the boundary node and its ghost
  *   max_iter     iteration cap of the local fixed-point solve for F (0: 100)
  *   tol          its tolerance, max|dF| <= tol * max(rho, |F|)
- *                (0: 1e-14 in FP64, 1e-6 in FP32; never below 64 ulp of |F|)
+ *                (0: 1e-14 in FP64, 1e-6 with FP32 arithmetic; never below 64 ulp of |F|)
  *   stream       cudaStream_t for all work of the simulation (NULL: default) */
 typedef struct {
   double tau;
@@ -111,6 +125,7 @@ typedef struct {
   int32_t max_iter;
   double tol;
   void *stream;
+  int32_t reference;
 } vlb_params;
 
 /* Per-mesh diagnostics filled by vlb_mesh_info. */
@@ -147,8 +162,9 @@ void vlb_mesh_destroy(vlb_mesh *mesh);
 /* Create a simulation on a mesh and set N_a = J f^eq_a(rho, U, U~ = U)
  * (Eqs. 14, 33) with U^i = u . g^i. rho [ncell] and u [ncell][dim] are host
  * arrays (Euclidean velocity). The mesh must outlive the simulation.
- * Errors: VLB_EINVAL (tau <= 1/2, bad precision or coef_mode, moving walls
- * on a cell touching two walls), VLB_ENOMEM, VLB_ECUDA. */
+ * Errors: VLB_EINVAL (tau <= 1/2, bad precision, coef_mode or reference,
+ * VLB_REF_REST without plane mode, moving walls on a cell touching two
+ * walls), VLB_ENOMEM, VLB_ECUDA. */
 int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, const double *u,
              vlb_sim **out);
 /* Re-initialise the populations from host fields as vlb_init does (no allocation). */

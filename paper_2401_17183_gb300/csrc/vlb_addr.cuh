@@ -80,22 +80,32 @@ struct Addr {
   }
 };
 
-// Arrived populations N_a(q, t). Even parity: slot a of q. Odd parity (the
-// layout an even step leaves behind): slot abar of q - c_a, or slot a of q
-// when q - c_a lies beyond a wall (halfway bounce-back).
-template <int Q, bool ODD, typename S, typename R, typename IT>
-__device__ __forceinline__ void pull(const S *__restrict__ f, IT ps, const Addr<Q, IT> &ad,
-                                     R (&N)[Q]) {
+// Storage location (slot, cell) of the arrived population N_a(q, t). Even
+// parity: slot a of q. Odd parity (the layout an even step leaves behind):
+// slot abar of q - c_a, or slot a of q when q - c_a lies beyond a wall
+// (halfway bounce-back).
+template <int Q, bool ODD, typename IT>
+__device__ __forceinline__ void arrived_loc(const Addr<Q, IT> &ad, int a, int &slot, IT &cell) {
+  if (!ODD || a == 0 || ad.crosses(a, -1)) {
+    slot = a;
+    cell = ad.cell;
+  } else {
+    slot = lat_opp<Q>(a);
+    cell = ad.nb(a, -1);
+  }
+}
+
+// Arrived populations N_a(q, t) themselves, in FP64: the stored deviation
+// plus the storage reference of its location.
+template <int Q, bool ODD, typename S, typename IT>
+__device__ __forceinline__ void pull_abs(const S *__restrict__ f, IT ps, const Addr<Q, IT> &ad,
+                                         const RefCtx &ref, double (&N)[Q]) {
 #pragma unroll
   for (int a = 0; a < Q; a++) {
-    if (!ODD || a == 0) {
-      N[a] = static_cast<R>(f[a * ps + ad.cell]);
-    } else {
-      if (ad.crosses(a, -1))
-        N[a] = static_cast<R>(f[a * ps + ad.cell]);
-      else
-        N[a] = static_cast<R>(f[lat_opp<Q>(a) * ps + ad.nb(a, -1)]);
-    }
+    int slot;
+    IT cell;
+    arrived_loc<Q, ODD, IT>(ad, a, slot, cell);
+    N[a] = load_s<double>(f[(IT)slot * ps + cell]) + ref_at<Q>(ref, slot, (int64_t)cell);
   }
 }
 

@@ -248,8 +248,10 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
   *out = nullptr;
   if (!mesh || !params || !rho || !u) return fail(VLB_EINVAL, "NULL argument");
   if (!(params->tau > 0.5)) return fail(VLB_EINVAL, "tau = %g must exceed 1/2", params->tau);
-  if (params->precision != VLB_F64 && params->precision != VLB_F32)
+  if (params->precision < VLB_F64 || params->precision > VLB_BF16)
     return fail(VLB_EINVAL, "unknown precision %d", params->precision);
+  if (params->reference != VLB_REF_UNIFORM && params->reference != VLB_REF_REST)
+    return fail(VLB_EINVAL, "unknown reference %d", params->reference);
   if (params->coef_mode < VLB_COEF_AUTO || params->coef_mode > VLB_COEF_PLANE)
     return fail(VLB_EINVAL, "unknown coef_mode %d", params->coef_mode);
   const int dim = mesh->md.dim, q = mesh->md.q;
@@ -283,11 +285,22 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
   }
   s->plane = plane ? 1 : 0;
   s->ncoef = plane ? mesh->ncell / mesh->md.n[dim - 1] : mesh->ncell;
-  const bool f64 = params->precision == VLB_F64;
+  const bool f16 = params->precision == VLB_F16 || params->precision == VLB_BF16;
+  if (params->reference == VLB_REF_REST && f16) {
+    if (!plane) {
+      delete s;
+      return fail(VLB_EINVAL,
+                  "reference REST needs plane mode (a geometry that does not vary along the fastest axis)");
+    }
+    s->ref_rest = 1;
+  }
+  const bool f64 = vlb::arith_f64(params->precision);
   s->nc = q == 9 ? (f64 ? vlb::CoefLayout<9>::stride<double>() : vlb::CoefLayout<9>::stride<float>())
                  : (f64 ? vlb::CoefLayout<19>::stride<double>() : vlb::CoefLayout<19>::stride<float>());
   const size_t es = f64 ? 8 : 4;
-  cudaError_t e = cudaMalloc(&s->d_f, es * q * mesh->ncell);
+  // 16 bytes of padding: a 16-bit population is read as the aligned 32-bit
+  // word that contains it
+  cudaError_t e = cudaMalloc(&s->d_f, vlb::storage_bytes(params->precision) * q * mesh->ncell + 16);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_coef, es * s->nc * s->ncoef);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
   if (e != cudaSuccess) {

@@ -310,6 +310,8 @@ struct PackArgs {
   double body[3];
   double wall_u[3][2][3];
   double wall_omega[3][2][3];
+  int32_t ref_rest;  // fill the storage-reference offsets (16-bit storage, plane mode)
+  double nref;
 };
 
 template <int Q, typename R>
@@ -343,6 +345,25 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
     CollideState<Q, double> cs;
     collide_cell<Q, double, false, false>(N, rec, 0.0, a.tau, 1e-15, 400, Np, cs);
     for (int i = 0; i < D; i++) rec[L::FR + i] = cs.conv ? cs.F[i] : 0.0;
+  }
+  // storage references: the rest state of Eq. 33 at the column that holds each
+  // location, as offsets from the uniform reference (the fastest axis never
+  // changes the column, so only the other axes decide a wall crossing)
+  if (a.ref_rest) {
+    const Addr<Q> ad0(a.g, c);
+    for (int av = 0; av < Q; av++) {
+      const double wn = lat_w<Q, double>(av) * a.nref;
+      rec[L::ROWN + av] = rest_ref<Q>(a.J[c], a.ginv + c * NS, av) - wn;
+      for (int sg = -1; sg <= 1; sg += 2) {
+        bool crs = false;
+        for (int ax = 0; ax < D - 1; ax++) {
+          const int cd = sg * Lat<Q>::c(av, ax);
+          if ((cd > 0 && ad0.hi[ax]) || (cd < 0 && ad0.lo[ax])) crs = true;
+        }
+        const int64_t cb = crs || av == 0 ? c : (ad0.nb(av, sg) / a.nfast) * a.nfast;
+        rec[(sg < 0 ? L::RIN : L::ROUT) + av] = rest_ref<Q>(a.J[cb], a.ginv + cb * NS, av) - wn;
+      }
+    }
   }
   R *out = coef + r * RS;
   for (int k = 0; k < RS; k++) out[k] = k < L::NC ? static_cast<R>(rec[k]) : R(0);
@@ -394,6 +415,8 @@ static cudaError_t pack_q(const vlb_sim *sim, cudaStream_t s) {
   a.nfast = m->md.n[m->md.dim - 1];
   a.plane = sim->plane;
   a.tau = sim->p.tau;
+  a.ref_rest = sim->ref_rest;
+  a.nref = sim->nref;
   for (int d = 0; d < 3; d++) a.body[d] = sim->p.body_force[d];
   for (int ax = 0; ax < 3; ax++)
     for (int sd = 0; sd < 2; sd++)
@@ -403,7 +426,7 @@ static cudaError_t pack_q(const vlb_sim *sim, cudaStream_t s) {
       }
   const int threads = 128;
   const int64_t blocks = (a.nrec + threads - 1) / threads;
-  if (sim->p.precision == VLB_F64)
+  if (arith_f64(sim->p.precision))
     k_pack_coef<Q, double><<<(unsigned)blocks, threads, 0, s>>>(a, (double *)sim->d_coef);
   else
     k_pack_coef<Q, float><<<(unsigned)blocks, threads, 0, s>>>(a, (float *)sim->d_coef);
@@ -418,7 +441,7 @@ cudaError_t launch_pack_coef(const vlb_sim *sim, cudaStream_t s) {
 // N_a = J f^eq_a(rho, U, U~ = U), U^i = u . g^i (Eqs. 14, 33), normal layout
 template <int Q, typename S>
 __global__ void k_init(const double *J, const double *gu, const double *ginv, const double *rho,
-                       const double *u, int64_t ncell, double nref, S *f) {
+                       const double *u, int64_t ncell, RefCtx ref, S *f) {
   constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
@@ -434,15 +457,14 @@ __global__ void k_init(const double *J, const double *gu, const double *ginv, co
   EqParts<Q, double> e;
   eq_parts<Q, double>(gd, U, zero, e);
   const double r = rho[c], Jc = J[c];
-  // stored as N_a - w_a n_ref
-  f[c] = static_cast<S>(Jc * r * lat_w<Q, double>(0) * eq_even<Q, double>(e, 0) -
-                        lat_w<Q, double>(0) * nref);
+  // stored relative to the storage reference of each location
+  f[c] = store_s<S>(Jc * r * lat_w<Q, double>(0) * eq_even<Q, double>(e, 0) - ref_at<Q>(ref, 0, c));
 #pragma unroll
   for (int p = 1; p <= H; p++) {
     const double E = eq_even<Q, double>(e, p), O = eq_odd<Q, double>(e, U, p);
     const double w = lat_w<Q, double>(p), rw = Jc * r * w;
-    f[p * ncell + c] = static_cast<S>(rw * (E + O) - w * nref);
-    f[(p + H) * ncell + c] = static_cast<S>(rw * (E - O) - w * nref);
+    f[p * ncell + c] = store_s<S>(rw * (E + O) - ref_at<Q>(ref, p, c));
+    f[(p + H) * ncell + c] = store_s<S>(rw * (E - O) - ref_at<Q>(ref, p + H, c));
   }
 }
 
@@ -450,23 +472,17 @@ cudaError_t launch_init(const vlb_sim *sim, const double *d_rho, const double *d
   const vlb_mesh *m = sim->mesh;
   const int threads = 128;
   const int64_t blocks = (m->ncell + threads - 1) / threads;
-  const bool f64 = sim->p.precision == VLB_F64;
-  if (m->md.q == 9) {
-    if (f64)
-      k_init<9, double><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u,
-                                                             m->ncell, sim->nref, (double *)sim->d_f);
+  const RefCtx ref = make_ref(sim);
+  return with_storage(sim->p.precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    if (m->md.q == 9)
+      k_init<9, S><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u, m->ncell,
+                                                        ref, (S *)sim->d_f);
     else
-      k_init<9, float><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u,
-                                                            m->ncell, sim->nref, (float *)sim->d_f);
-  } else {
-    if (f64)
-      k_init<19, double><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho,
-                                                              d_u, m->ncell, sim->nref, (double *)sim->d_f);
-    else
-      k_init<19, float><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u,
-                                                             m->ncell, sim->nref, (float *)sim->d_f);
-  }
-  return cudaGetLastError();
+      k_init<19, S><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u, m->ncell,
+                                                         ref, (S *)sim->d_f);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace vlb

@@ -3,6 +3,8 @@
 // declarations). Not part of the public C-ABI (include/vlb.h).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,7 +117,15 @@ struct CoefLayout {
   static constexpr int PO2 = PE + D * NS;      // D x NO: coefficient of (U~^k)^2 U~^l (k != l)
   static constexpr int LO = PO2 + D * NO;      // D x D: coefficient of U~
   static constexpr int TL = LO + D * D;        // D x D: coefficient of J F
-  static constexpr int NC = TL + D * D;
+  // storage references of 16-bit populations (reference VLB_REF_REST, plane
+  // mode), as offsets from the uniform reference, r - w_a n_ref: at the cell's
+  // own locations, at the location each population of an odd step is read
+  // from (slot abar of q - c_a), and at the one it is written to (slot a of
+  // q + c_a); a link through a wall reads and writes the cell's own slot
+  static constexpr int ROWN = round4(TL + D * D);
+  static constexpr int RIN = ROWN + Q;
+  static constexpr int ROUT = RIN + Q;
+  static constexpr int NC = ROUT + Q;
   __host__ __device__ static constexpr int mp(int p, int i) { return MPD + (p - 1) * 2 * D + i; }
   __host__ __device__ static constexpr int dk(int p, int i) { return MPD + (p - 1) * 2 * D + D + i; }
   // record stride in elements of type R: a multiple of four elements, so that
@@ -135,6 +145,48 @@ __device__ __forceinline__ R maxnan(R a, R b) {
 }
 __device__ __forceinline__ float absr(float x) { return fabsf(x); }
 __device__ __forceinline__ double absr(double x) { return fabs(x); }
+
+// population storage types: FP64, FP32, IEEE half, bfloat16
+template <typename R, typename S>
+__device__ __forceinline__ R load_s(S x) {
+  return static_cast<R>(x);
+}
+template <>
+__device__ __forceinline__ float load_s<float, __half>(__half x) {
+  return __half2float(x);
+}
+template <>
+__device__ __forceinline__ double load_s<double, __half>(__half x) {
+  return (double)__half2float(x);
+}
+template <>
+__device__ __forceinline__ float load_s<float, __nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <>
+__device__ __forceinline__ double load_s<double, __nv_bfloat16>(__nv_bfloat16 x) {
+  return (double)__bfloat162float(x);
+}
+template <typename S, typename R>
+__device__ __forceinline__ S store_s(R x) {
+  return static_cast<S>(x);
+}
+template <>
+__device__ __forceinline__ __half store_s<__half, float>(float x) {
+  return __float2half_rn(x);
+}
+template <>
+__device__ __forceinline__ __half store_s<__half, double>(double x) {
+  return __double2half(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_s<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_s<__nv_bfloat16, double>(double x) {
+  return __double2bfloat16(x);
+}
 
 // --------------------------------------------------------------------------
 // Equilibrium of Eq. 33 for one cell, specialised to velocity sets whose
@@ -255,6 +307,45 @@ __device__ __forceinline__ R eq_odd(const EqParts<Q, R> &e, const R (&U)[Lat<Q>:
   return R(3) * cu + R(4.5) * cc;
 }
 
+// Storage reference of population a at a cell: with VLB_REF_REST the rest
+// state of Eq. 33 on the cell's metric, J w_a (1 + even part at U = 0), rounded
+// to FP32 (every kernel that stores or reads 16-bit populations uses this one
+// value); else w_a n_ref. ginv is the cell's packed g^ij.
+template <int Q>
+__device__ __forceinline__ double rest_ref(double J, const double *ginv, int a) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2;
+  double gd[NS], z[D];
+#pragma unroll
+  for (int i = 0; i < NS; i++) gd[i] = ginv[i];
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    gd[sym<D>(i, i)] -= 1.0;
+    z[i] = 0.0;
+  }
+  EqParts<Q, double> e;
+  eq_parts<Q, double>(gd, z, z, e);
+  const int p = a <= Lat<Q>::H ? a : a - Lat<Q>::H;
+  return (double)(float)(J * lat_w<Q, double>(a) * eq_even<Q, double>(e, p));
+}
+
+// Where the storage reference of a location comes from (kernels outside the
+// time step, which read populations by location).
+struct RefCtx {
+  int32_t rest;          // VLB_REF_REST in use
+  double nref;           // uniform reference
+  const double *J;       // FP64 geometry (rest)
+  const double *ginv;
+  int64_t nfast;         // plane mode: a column's geometry is that of its first cell
+};
+
+template <int Q>
+__device__ __forceinline__ double ref_at(const RefCtx &r, int slot, int64_t cell) {
+  if (!r.rest) return lat_w<Q, double>(slot) * r.nref;
+  constexpr int NS = Lat<Q>::D * (Lat<Q>::D + 1) / 2;
+  const int64_t c0 = (cell / r.nfast) * r.nfast;
+  return rest_ref<Q>(r.J[c0], r.ginv + c0 * NS, slot);
+}
+
 // --------------------------------------------------------------------------
 // Mesh and simulation objects (host side).
 struct MeshDev {
@@ -296,6 +387,7 @@ struct vlb_sim {
   int32_t plane = 0;
   int64_t t = 0;
   double nref = 0.0;          // populations are stored as N_a - w_a nref, nref = rho_0 J_ref
+  int32_t ref_rest = 0;       // 16-bit storage relative to the local rest state
   int *d_err = nullptr;       // sticky kernel error flags
   double *d_fields = nullptr; // moments output staging [ncell][1 + 2 dim]
   double *d_partial = nullptr;
@@ -306,6 +398,36 @@ struct vlb_sim {
 };
 
 namespace vlb {
+
+// storage type of a precision, as a type tag for generic host dispatch
+template <typename T>
+struct TypeTag {
+  using type = T;
+};
+template <typename F>
+inline auto with_storage(int32_t precision, F &&fn) {
+  switch (precision) {
+    case VLB_F64: return fn(TypeTag<double>{});
+    case VLB_F16: return fn(TypeTag<__half>{});
+    case VLB_BF16: return fn(TypeTag<__nv_bfloat16>{});
+    default: return fn(TypeTag<float>{});
+  }
+}
+inline size_t storage_bytes(int32_t precision) {
+  return precision == VLB_F64 ? 8 : precision == VLB_F32 ? 4 : 2;
+}
+// arithmetic (and coefficient) type: FP64 only for VLB_F64
+inline bool arith_f64(int32_t precision) { return precision == VLB_F64; }
+
+inline RefCtx make_ref(const vlb_sim *sim) {
+  RefCtx r;
+  r.rest = sim->ref_rest;
+  r.nref = sim->nref;
+  r.J = sim->mesh->d_J;
+  r.ginv = sim->mesh->d_ginv;
+  r.nfast = sim->plane ? sim->mesh->md.n[sim->mesh->md.dim - 1] : 1;
+  return r;
+}
 
 // error flags raised by kernels
 enum : int { ERR_NOCONV = 1, ERR_NONFINITE = 2, ERR_GEOM = 4 };

@@ -17,7 +17,7 @@ struct MomArgs {
   int32_t has_rot[3];
   int32_t periodic[3];
   double tau;
-  double nref;
+  RefCtx ref;
   int *err;
 };
 
@@ -58,9 +58,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
        c += (int64_t)gridDim.x * blockDim.x) {
     const Addr<Q> ad(a.g, c);
     double N[Q];
-    pull<Q, ODD, S, double>(f, a.ncell, ad, N);
-#pragma unroll
-    for (int av = 0; av < Q; av++) N[av] += lat_w<Q, double>(av) * a.nref;
+    pull_abs<Q, ODD, S>(f, a.ncell, ad, a.ref, N);
     double K[Q][D], G[D], rec[CoefLayout<Q>::NC];
     for (int av = 0; av < Q; av++)
       for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
@@ -162,7 +160,7 @@ static cudaError_t moments_t(const vlb_sim *sim, double *d_out, double *d_partia
     for (int k = 0; k < 9; k++) a.rot[d][k] = m->md.rot[d][k];
   }
   a.tau = sim->p.tau;
-  a.nref = sim->nref;
+  a.ref = make_ref(sim);
   a.err = sim->d_err;
   if (sim->t & 1)
     k_moments<Q, S, true><<<(unsigned)nblk, kMomThreads, 0, s>>>(a, d_out, d_partial);
@@ -173,12 +171,11 @@ static cudaError_t moments_t(const vlb_sim *sim, double *d_out, double *d_partia
 
 cudaError_t launch_moments(const vlb_sim *sim, double *d_out, double *d_partial, int64_t nblk,
                            cudaStream_t s) {
-  const bool f64 = sim->p.precision == VLB_F64;
-  if (sim->mesh->md.q == 9)
-    return f64 ? moments_t<9, double>(sim, d_out, d_partial, nblk, s)
-               : moments_t<9, float>(sim, d_out, d_partial, nblk, s);
-  return f64 ? moments_t<19, double>(sim, d_out, d_partial, nblk, s)
-             : moments_t<19, float>(sim, d_out, d_partial, nblk, s);
+  return with_storage(sim->p.precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    return sim->mesh->md.q == 9 ? moments_t<9, S>(sim, d_out, d_partial, nblk, s)
+                                : moments_t<19, S>(sim, d_out, d_partial, nblk, s);
+  });
 }
 
 // fixed-order reduction of the per-block partial sums (deterministic)
@@ -198,61 +195,62 @@ cudaError_t launch_finish_totals(const double *d_partial, int64_t nblk, double *
 
 // ------------------------------------------------------------------ state gather / scatter
 template <int Q, typename S, bool ODD>
-__global__ void k_get_state(const S *f, Grid g, int64_t ncell, double nref, double *N_out) {
+__global__ void k_get_state(const S *f, Grid g, int64_t ncell, RefCtx ref, double *N_out) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const Addr<Q> ad(g, c);
   double N[Q];
-  pull<Q, ODD, S, double>(f, ncell, ad, N);
+  pull_abs<Q, ODD, S>(f, ncell, ad, ref, N);
 #pragma unroll
-  for (int a = 0; a < Q; a++) N_out[a * ncell + c] = N[a] + lat_w<Q, double>(a) * nref;
+  for (int a = 0; a < Q; a++) N_out[a * ncell + c] = N[a];
 }
 
+// writes the even-parity layout (slot a of q holds N_a(q))
 template <int Q, typename S>
-__global__ void k_set_state(S *f, int64_t ncell, double nref, const double *N_in) {
+__global__ void k_set_state(S *f, int64_t ncell, RefCtx ref, const double *N_in) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
 #pragma unroll
-  for (int a = 0; a < Q; a++)
-    f[a * ncell + c] = static_cast<S>(N_in[a * ncell + c] - lat_w<Q, double>(a) * nref);
+  for (int a = 0; a < Q; a++) f[a * ncell + c] = store_s<S>(N_in[a * ncell + c] - ref_at<Q>(ref, a, c));
 }
 
-template <int Q, typename S>
-static cudaError_t get_t(const vlb_sim *sim, double *d_N, cudaStream_t s) {
+cudaError_t launch_get_state(const vlb_sim *sim, double *d_N, cudaStream_t s) {
   const vlb_mesh *m = sim->mesh;
   const int threads = 256;
   const int64_t blocks = (m->ncell + threads - 1) / threads;
   const Grid g = make_grid(m);
-  if (sim->t & 1)
-    k_get_state<Q, S, true><<<(unsigned)blocks, threads, 0, s>>>((const S *)sim->d_f, g, m->ncell, sim->nref, d_N);
-  else
-    k_get_state<Q, S, false><<<(unsigned)blocks, threads, 0, s>>>((const S *)sim->d_f, g, m->ncell, sim->nref, d_N);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_get_state(const vlb_sim *sim, double *d_N, cudaStream_t s) {
-  const bool f64 = sim->p.precision == VLB_F64;
-  if (sim->mesh->md.q == 9) return f64 ? get_t<9, double>(sim, d_N, s) : get_t<9, float>(sim, d_N, s);
-  return f64 ? get_t<19, double>(sim, d_N, s) : get_t<19, float>(sim, d_N, s);
+  const RefCtx ref = make_ref(sim);
+  return with_storage(sim->p.precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    const S *f = (const S *)sim->d_f;
+    if (m->md.q == 9) {
+      if (sim->t & 1)
+        k_get_state<9, S, true><<<(unsigned)blocks, threads, 0, s>>>(f, g, m->ncell, ref, d_N);
+      else
+        k_get_state<9, S, false><<<(unsigned)blocks, threads, 0, s>>>(f, g, m->ncell, ref, d_N);
+    } else {
+      if (sim->t & 1)
+        k_get_state<19, S, true><<<(unsigned)blocks, threads, 0, s>>>(f, g, m->ncell, ref, d_N);
+      else
+        k_get_state<19, S, false><<<(unsigned)blocks, threads, 0, s>>>(f, g, m->ncell, ref, d_N);
+    }
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_set_state(const vlb_sim *sim, const double *d_N, cudaStream_t s) {
   const vlb_mesh *m = sim->mesh;
   const int threads = 256;
   const int64_t blocks = (m->ncell + threads - 1) / threads;
-  const bool f64 = sim->p.precision == VLB_F64;
-  if (m->md.q == 9) {
-    if (f64)
-      k_set_state<9, double><<<(unsigned)blocks, threads, 0, s>>>((double *)sim->d_f, m->ncell, sim->nref, d_N);
+  const RefCtx ref = make_ref(sim);
+  return with_storage(sim->p.precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    if (m->md.q == 9)
+      k_set_state<9, S><<<(unsigned)blocks, threads, 0, s>>>((S *)sim->d_f, m->ncell, ref, d_N);
     else
-      k_set_state<9, float><<<(unsigned)blocks, threads, 0, s>>>((float *)sim->d_f, m->ncell, sim->nref, d_N);
-  } else {
-    if (f64)
-      k_set_state<19, double><<<(unsigned)blocks, threads, 0, s>>>((double *)sim->d_f, m->ncell, sim->nref, d_N);
-    else
-      k_set_state<19, float><<<(unsigned)blocks, threads, 0, s>>>((float *)sim->d_f, m->ncell, sim->nref, d_N);
-  }
-  return cudaGetLastError();
+      k_set_state<19, S><<<(unsigned)blocks, threads, 0, s>>>((S *)sim->d_f, m->ncell, ref, d_N);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace vlb

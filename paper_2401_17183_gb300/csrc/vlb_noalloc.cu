@@ -32,7 +32,7 @@ struct TotArgs {
   int64_t ncell;
   int64_t per_block;
   const double *gl;
-  double nref;
+  RefCtx ref;
   double rot[3][9];
   int32_t has_rot[3];
   int32_t periodic[3];
@@ -75,13 +75,13 @@ __global__ void __launch_bounds__(kNaThreads) k_totals_noalloc(const TotArgs a, 
   for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     const Addr<Q> ad(a.g, c);
     double N[Q];
-    pull<Q, ODD, S, double>(f, a.ncell, ad, N);
+    pull_abs<Q, ODD, S>(f, a.ncell, ad, a.ref, N);
     double gl[D][D];
     for (int i = 0; i < D; i++)
       for (int d = 0; d < D; d++) gl[i][d] = a.gl[(c * D + i) * D + d];
 #pragma unroll 1
     for (int av = 0; av < Q; av++) {
-      const double n = N[av] + lat_w<Q, double>(av) * a.nref;
+      const double n = N[av];
       double e[D], eb[D];
       for (int d = 0; d < D; d++) {
         double s = 0.0;
@@ -167,7 +167,7 @@ cudaError_t launch_na(const vlb_sim *sim, double *scratch, int64_t nblk, double 
   a.ncell = m->ncell;
   a.per_block = kNaCellsPerBlock;
   a.gl = m->d_gl;
-  a.nref = sim->nref;
+  a.ref = make_ref(sim);
   for (int d = 0; d < 3; d++) {
     a.has_rot[d] = m->md.has_rot[d];
     a.periodic[d] = (d < m->md.dim && m->md.bc[d] == VLB_PERIODIC) ? 1 : 0;
@@ -203,13 +203,11 @@ extern "C" int vlb_totals_noalloc(vlb_sim *sim, double *d_totals) {
   if (e != cudaSuccess)
     return vlb::set_error(VLB_ECUDA, "vlb_totals_noalloc: cudaGetSymbolAddress: %s",
                           cudaGetErrorString(e));
-  const bool f64 = sim->p.precision == VLB_F64;
-  if (m->md.q == 9)
-    e = f64 ? vlb::launch_na<9, double>(sim, scratch, nblk, d_totals)
-            : vlb::launch_na<9, float>(sim, scratch, nblk, d_totals);
-  else
-    e = f64 ? vlb::launch_na<19, double>(sim, scratch, nblk, d_totals)
-            : vlb::launch_na<19, float>(sim, scratch, nblk, d_totals);
+  e = vlb::with_storage(sim->p.precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    return m->md.q == 9 ? vlb::launch_na<9, S>(sim, scratch, nblk, d_totals)
+                        : vlb::launch_na<19, S>(sim, scratch, nblk, d_totals);
+  });
   if (e != cudaSuccess)
     return vlb::set_error(VLB_ECUDA, "vlb_totals_noalloc: launch: %s", cudaGetErrorString(e));
   return VLB_OK;

@@ -1,0 +1,383 @@
+// vlb_step.cuh -- the fused stream-and-collide time step (Eq. 12 with the
+// one-to-one advection of Eq. 22), one thread per cell, in place with the A-A
+// access pattern over a structure-of-arrays population layout f[a][cell]:
+//
+//   even step: read N_a(q) from slot a of q; collide; write N'_a(q) to slot
+//              abar of q (no neighbour access at all).
+//   odd step : the population arriving at q along c_a is N'_a(q - c_a), which
+//              the previous even step left in slot abar of q - c_a; collide;
+//              write N'_a(q) to slot a of q + c_a, where the next even step
+//              reads it as N_a(q + c_a).
+//
+// Each thread writes exactly the locations it read, so no two threads touch
+// the same word. Walls (index-space halfway bounce-back) fold into the same
+// addressing: a population that would leave through a wall is written to the
+// cell's own slot that the next step reads as the reflected arrival.
+//
+// The kernel is persistent: each block walks a contiguous run of tiles (128
+// consecutive cells along the fastest axis), and each thread copies the Q
+// populations of its cell in tile k + 2 into shared memory with asynchronous
+// copies while it collides its cell in tile k (three stages). The DRAM latency
+// of the reads is thereby hidden behind the arithmetic of a tile without
+// holding the loads in registers. In plane mode the tile's shared coefficient
+// record travels in the same copy group, in 16-byte pieces; one block barrier
+// per tile makes those pieces visible to every thread and guards the reuse of
+// a stage. Since the read and write sets of different cells are disjoint,
+// reading tile k + 2 ahead of the writes of tile k is safe.
+//
+// Populations may be stored in 16 bits (IEEE half or bfloat16) with FP32
+// arithmetic: each value is staged as the aligned 32-bit word that contains
+// it and the thread remembers which half it is.
+#pragma once
+
+#include <mutex>
+#include <tuple>
+#include <type_traits>
+#include <vector>
+
+#include "vlb_addr.cuh"
+#include "vlb_collide.cuh"
+
+namespace vlb {
+
+struct StepArgs {
+  void *f;
+  const void *coef;
+  int *err;
+  Grid g;
+  int64_t ncell;
+  int32_t plane;    // one coefficient record per column of the fastest axis
+  double tau, tol;
+  double nref;      // populations are stored as N_a - w_a nref
+  int32_t max_iter;
+  int32_t moving;
+  // tiles: index t = (A nB + B) ntf + tf over the two slow axes (A, B) and
+  // the tiles tf of the fastest axis; 3D: (A, B) = (i0, i1); 2D: (0, i0)
+  int64_t ntiles;
+  int32_t ntf, nA, nB;
+  int64_t per_block;  // tiles per block (contiguous runs)
+};
+
+constexpr int kStepThreads = 128;
+
+// asynchronous global -> shared copies of one element (4 or 8 bytes)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *sdst, const void *gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// position of a tile in the (A, B, tf) mixed radix
+struct TileCursor {
+  int32_t A, B, tf;
+  __device__ __forceinline__ void set(int64_t t, const StepArgs &a) {
+    tf = (int32_t)(t % a.ntf);
+    const int64_t r = t / a.ntf;
+    B = (int32_t)(r % a.nB);
+    A = (int32_t)(r / a.nB);
+  }
+  __device__ __forceinline__ void next(const StepArgs &a) {
+    if (++tf == a.ntf) {
+      tf = 0;
+      if (++B == a.nB) {
+        B = 0;
+        ++A;
+      }
+    }
+  }
+};
+
+template <int Q, typename IT>
+__device__ __forceinline__ Addr<Q, IT> tile_addr(const Grid &g, const TileCursor &c, IT ifast) {
+  return Lat<Q>::D == 3 ? Addr<Q, IT>(g, (IT)c.A, (IT)c.B, ifast) : Addr<Q, IT>(g, (IT)c.B, ifast, (IT)0);
+}
+
+// index of the arrived population N_a(q, t) (the A-A read side): slot a of q
+// (even parity, the rest population, or a link that comes back from a wall)
+// or slot abar of q - c_a
+template <int Q, bool ODD, typename IT>
+__device__ __forceinline__ IT src_index(IT ps, const Addr<Q, IT> &ad, int a) {
+  if (!ODD || a == 0 || ad.crosses(a, -1)) return (IT)a * ps + ad.cell;
+  return (IT)lat_opp<Q>(a) * ps + ad.nb(a, -1);
+}
+
+template <typename R>
+constexpr int step_min_blocks() {
+  return sizeof(R) == 4 ? 4 : 2;
+}
+
+// pipeline depth: tiles whose copies are in flight while one is collided
+constexpr int kStages = 3;
+
+// Shared memory of one block: per stage, the populations of its 128 cells and,
+// in plane mode, the coefficient record they all share. A 16-bit population
+// is staged as the aligned 32-bit word that holds it (asynchronous copies move
+// 4, 8 or 16 bytes), with one bit per direction saying which half it is.
+template <int Q, typename S, typename R>
+struct StepSmem {
+  static constexpr int RS = CoefLayout<Q>::template stride<R>();
+  static constexpr bool H16 = sizeof(S) == 2;
+  using PopT = typename std::conditional<H16, uint32_t, S>::type;
+  alignas(16) R rec[kStages][RS];
+  PopT pop[kStages][Q][kStepThreads];
+  uint32_t half_hi[H16 ? kStages : 1][kStepThreads];
+};
+
+// a 16-bit storage value from its bit pattern
+template <typename S>
+__device__ __forceinline__ S s16_from_bits(unsigned short b);
+template <>
+__device__ __forceinline__ __half s16_from_bits<__half>(unsigned short b) {
+  return __ushort_as_half(b);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 s16_from_bits<__nv_bfloat16>(unsigned short b) {
+  return __ushort_as_bfloat16(b);
+}
+
+// REFOFS: 16-bit populations stored relative to the local rest state (the
+// offsets from the uniform reference come with the record, plane mode only).
+template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, typename IT>
+__global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(const StepArgs a) {
+  constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  using L = CoefLayout<Q>;
+  constexpr int RS = L::template stride<R>();
+  constexpr bool H16 = sizeof(S) == 2;
+  static_assert(!REFOFS || (PLANE && H16), "storage offsets need plane mode and 16-bit storage");
+  // 16-byte pieces of the record that the kernel reads
+  constexpr int RCHUNK = (REFOFS ? RS : L::ROWN) * (int)sizeof(R) / 16;
+  static_assert(RCHUNK <= kStepThreads, "record larger than one copy per thread");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<Q, S, R> &sm = *reinterpret_cast<StepSmem<Q, S, R> *>(smem_raw);
+  const int64_t t0 = (int64_t)blockIdx.x * a.per_block;
+  const int64_t t1 = t0 + a.per_block < a.ntiles ? t0 + a.per_block : a.ntiles;
+  if (t0 >= t1) return;
+  S *__restrict__ f = static_cast<S *>(a.f);
+  const R *__restrict__ coef = static_cast<const R *>(a.coef);
+  const IT ps = (IT)a.ncell;
+  const IT nfast = (IT)(D == 3 ? a.g.n[2] : a.g.n[1]);
+  const int tid = threadIdx.x;
+
+  // issue this thread's copies for tile c into stage st: the populations of
+  // its cell and, in plane mode, one 16-byte piece of the shared record
+  auto prefetch = [&](const TileCursor &c, int st) {
+    const IT ifast = (IT)c.tf * kStepThreads + (IT)tid;
+    if (ifast < nfast) {
+      const Addr<Q, IT> ad = tile_addr<Q, IT>(a.g, c, ifast);
+      if constexpr (H16) {
+        uint32_t hi = 0;
+#pragma unroll
+        for (int av = 0; av < Q; av++) {
+          const IT idx = src_index<Q, ODD, IT>(ps, ad, av);
+          cp_async<4>(&sm.pop[st][av][tid], reinterpret_cast<const uint32_t *>(f) + (idx >> 1));
+          hi |= (uint32_t)(idx & 1) << av;
+        }
+        sm.half_hi[st][tid] = hi;
+      } else {
+#pragma unroll
+        for (int av = 0; av < Q; av++)
+          cp_async<sizeof(S)>(&sm.pop[st][av][tid], f + src_index<Q, ODD, IT>(ps, ad, av));
+      }
+    }
+    if (PLANE && tid < RCHUNK) {
+      const int64_t rec = (int64_t)c.A * a.nB + c.B;
+      cp_async<16>(reinterpret_cast<unsigned char *>(&sm.rec[st][0]) + 16 * tid,
+                   reinterpret_cast<const unsigned char *>(coef + rec * RS) + 16 * tid);
+    }
+  };
+
+  // prologue: tiles t0 .. t0 + kStages - 2, one copy group each
+  TileCursor cur, nxt;
+  cur.set(t0, a);
+  nxt = cur;
+#pragma unroll
+  for (int k = 0; k < kStages - 1; k++) {
+    if (t0 + k < t1) prefetch(nxt, k);
+    cp_async_commit();
+    nxt.next(a);
+  }
+  int st = 0;
+  for (int64_t t = t0; t < t1; t++) {
+    // the copies of tile t (this thread's) are complete; after the barrier
+    // every thread's are, and every thread is done with tile t - 1, whose
+    // stage the next prefetch reuses
+    cp_async_wait<kStages - 2>();
+    __syncthreads();
+    {
+      int sn = st + kStages - 1;
+      if (sn >= kStages) sn -= kStages;
+      if (t + kStages - 1 < t1) prefetch(nxt, sn);
+      cp_async_commit();
+      nxt.next(a);
+    }
+
+    const IT ifast = (IT)cur.tf * kStepThreads + (IT)tid;
+    if (ifast < nfast) {
+      const Addr<Q, IT> ad = tile_addr<Q, IT>(a.g, cur, ifast);
+      const IT cell = ad.cell;
+      // ---- pull (read side of Eq. 22): deviations d_a = N_a - w_a n_ref
+      // ---- coefficients: in plane mode one record per column of the fastest
+      // axis, shared by the tile and staged in shared memory; else one per cell
+      const R *__restrict__ rc = PLANE ? &sm.rec[st][0] : coef + (int64_t)cell * RS;
+
+      R N[Q];
+      if constexpr (H16) {
+        const uint32_t hi = sm.half_hi[st][tid];
+#pragma unroll
+        for (int av = 0; av < Q; av++) {
+          const uint32_t w = sm.pop[st][av][tid];
+          const unsigned short b = (unsigned short)(((hi >> av) & 1) ? (w >> 16) : (w & 0xffffu));
+          N[av] = load_s<R>(s16_from_bits<S>(b));
+          if constexpr (REFOFS) {
+            // back to the uniform reference: add the storage offset of the location
+            const bool own = !ODD || av == 0 || ad.crosses(av, -1);
+            N[av] += rc[(own ? L::ROWN : L::RIN) + av];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int av = 0; av < Q; av++) N[av] = static_cast<R>(sm.pop[st][av][tid]);
+      }
+
+      // ---- collide (section 2.2)
+      R Np[Q];
+      CollideState<Q, R> cst;
+      collide_cell<Q, R, true, true>(N, rc, R(a.nref), R(a.tau), R(a.tol), a.max_iter, Np, cst);
+      if (!cst.conv) atomicOr(a.err, ERR_NOCONV);
+
+      // ---- moving walls: a reflected population is corrected by
+      //      -J rho [f^eq_a - f^eq_abar](rho = 1, U = U~ = U_wall)
+      const bool moving = a.moving && ad.wall_cell();
+      R uw[D];
+#pragma unroll
+      for (int i = 0; i < D; i++) uw[i] = moving ? rc[L::UW + i] : R(0);
+      EqParts<Q, R> ew;
+      if (moving) {
+        R zero[D], gd[L::NS];
+#pragma unroll
+        for (int i = 0; i < D; i++) zero[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < L::NS; i++) gd[i] = rc[L::GINV + i];
+        eq_parts<Q, R>(gd, uw, zero, ew);
+      }
+      const R Jc = moving ? rc[L::J] : R(0);
+
+      // ---- push (write side of Eq. 22)
+#pragma unroll
+      for (int av = 1; av < Q; av++) {
+        const int ab = lat_opp<Q>(av);
+        const bool crs = ad.crosses(av, 1);
+        R v = Np[av];
+        if (moving && crs) {
+          const int p = av <= H ? av : av - H;
+          const R O = eq_odd<Q, R>(ew, uw, p);
+          const R corr = R(2) * Jc * cst.rho * lat_w<Q, R>(av) * O;
+          v -= (av <= H) ? corr : -corr;
+        }
+        if constexpr (REFOFS) v -= rc[((!ODD || crs) ? L::ROWN : L::ROUT) + av];
+        if (!ODD || crs)
+          f[(IT)ab * ps + cell] = store_s<S>(v);
+        else
+          f[(IT)av * ps + ad.nb(av, 1)] = store_s<S>(v);
+      }
+      f[cell] = store_s<S>(REFOFS ? Np[0] - rc[L::ROWN] : Np[0]);
+    }
+    cur.next(a);
+    if (++st == kStages) st = 0;
+  }
+  cp_async_wait<0>();
+}
+
+// blocks the persistent kernel can keep resident on the current device
+// (queried once per kernel and device)
+static int resident_blocks(const void *kern, size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::tuple<const void *, int, int>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto &e : cache)
+    if (std::get<0>(e) == kern && std::get<1>(e) == dev) return std::get<2>(e);
+  int nb = 0, nsm = 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStepThreads, smem);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int total = (nb > 0 ? nb : 1) * (nsm > 0 ? nsm : 1);
+  cache.emplace_back(kern, dev, total);
+  return total;
+}
+
+template <int Q, typename S, typename R>
+cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
+  const vlb_mesh *m = sim->mesh;
+  StepArgs a;
+  a.f = sim->d_f;
+  a.coef = sim->d_coef;
+  a.err = sim->d_err;
+  a.g = make_grid(m);
+  a.ncell = m->ncell;
+  a.plane = sim->plane;
+  a.tau = sim->p.tau;
+  a.tol = sim->p.tol;
+  a.nref = sim->nref;
+  a.max_iter = sim->p.max_iter;
+  a.moving = 0;
+  for (int ax = 0; ax < 3; ax++)
+    for (int sd = 0; sd < 2; sd++)
+      for (int d = 0; d < 3; d++)
+        if (sim->p.wall_u[ax][sd][d] != 0.0 || sim->p.wall_omega[ax][sd][d] != 0.0) a.moving = 1;
+  const int dim = m->md.dim;
+  const int64_t nfast = dim == 3 ? m->md.n[2] : m->md.n[1];
+  a.ntf = (int32_t)((nfast + kStepThreads - 1) / kStepThreads);
+  a.nA = (int32_t)(dim == 3 ? m->md.n[0] : 1);
+  a.nB = (int32_t)(dim == 3 ? m->md.n[1] : m->md.n[0]);
+  a.ntiles = (int64_t)a.ntf * a.nA * a.nB;
+  // 32-bit indexing when every population offset fits
+  const bool i32 = (int64_t)Q * m->ncell < ((int64_t)1 << 31);
+  if (a.ntiles == 0) return cudaSuccess;
+  const size_t smem = sizeof(StepSmem<Q, S, R>);
+  auto go = [&](void (*kern)(StepArgs)) {
+    const int64_t nblk_max = resident_blocks(reinterpret_cast<const void *>(kern), smem);
+    a.per_block = (a.ntiles + nblk_max - 1) / nblk_max;
+    const int64_t nblk = (a.ntiles + a.per_block - 1) / a.per_block;
+    kern<<<(unsigned)nblk, kStepThreads, smem, s>>>(a);
+  };
+  auto pick = [&](auto plane_tag, auto ref_tag) {
+    constexpr bool P = decltype(plane_tag)::value, RO = decltype(ref_tag)::value;
+    if (i32) {
+      if (odd)
+        go(k_step<Q, S, R, true, P, RO, int32_t>);
+      else
+        go(k_step<Q, S, R, false, P, RO, int32_t>);
+    } else {
+      if (odd)
+        go(k_step<Q, S, R, true, P, RO, int64_t>);
+      else
+        go(k_step<Q, S, R, false, P, RO, int64_t>);
+    }
+  };
+  if constexpr (sizeof(S) == 2) {
+    if (a.plane && sim->ref_rest)
+      pick(std::true_type{}, std::true_type{});
+    else if (a.plane)
+      pick(std::true_type{}, std::false_type{});
+    else
+      pick(std::false_type{}, std::false_type{});
+  } else {
+    if (a.plane)
+      pick(std::true_type{}, std::false_type{});
+    else
+      pick(std::false_type{}, std::false_type{});
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vlb

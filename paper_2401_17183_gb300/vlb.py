@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "libvlb.so")
 VLB_OK, VLB_EINVAL, VLB_EGEOM, VLB_ENOCONV, VLB_ENOMEM, VLB_ECUDA, VLB_ENONFINITE = range(7)
 VLB_D2Q9, VLB_D3Q19 = 9, 19
 VLB_PERIODIC, VLB_WALL = 0, 1
-VLB_F64, VLB_F32 = 0, 1
+VLB_F64, VLB_F32, VLB_F16, VLB_BF16 = 0, 1, 2, 3
+VLB_REF_UNIFORM, VLB_REF_REST = 0, 1
 VLB_COEF_AUTO, VLB_COEF_FULL, VLB_COEF_PLANE = 0, 1, 2
 VLB_WALL_LINKS_ZERO, VLB_WALL_LINKS_GHOST = 0, 1
 _CODES = {1: "EINVAL", 2: "EGEOM", 3: "ENOCONV", 4: "ENOMEM", 5: "ECUDA", 6: "ENONFINITE"}
@@ -39,7 +40,7 @@ class vlb_params(C.Structure):
     _fields_ = [("tau", C.c_double), ("precision", C.c_int32), ("coef_mode", C.c_int32),
                 ("body_force", C.c_double * 3), ("wall_u", ((C.c_double * 3) * 2) * 3),
                 ("wall_omega", ((C.c_double * 3) * 2) * 3), ("max_iter", C.c_int32),
-                ("tol", C.c_double), ("stream", C.c_void_p)]
+                ("tol", C.c_double), ("stream", C.c_void_p), ("reference", C.c_int32)]
 
 
 class vlb_mesh_stats(C.Structure):
@@ -108,7 +109,8 @@ def lattice(q):
     return c, w
 
 
-def make_params(params, precision=VLB_F64, coef_mode=VLB_COEF_AUTO, stream=None):
+def make_params(params, precision=VLB_F64, coef_mode=VLB_COEF_AUTO, stream=None,
+                reference=VLB_REF_UNIFORM):
     p = vlb_params()
     p.tau = float(params["tau"])
     p.precision = int(precision)
@@ -128,6 +130,7 @@ def make_params(params, precision=VLB_F64, coef_mode=VLB_COEF_AUTO, stream=None)
     p.max_iter = int(params.get("max_iter", 0))
     p.tol = float(params.get("tol", 0.0))
     p.stream = stream
+    p.reference = int(reference)
     return p
 
 
@@ -189,10 +192,10 @@ class Sim:
     """vlb_init / vlb_step / vlb_moments / vlb_get_state / vlb_set_state / vlb_destroy."""
 
     def __init__(self, mesh, params, rho, u, precision=VLB_F64, coef_mode=VLB_COEF_AUTO,
-                 stream=None):
+                 stream=None, reference=VLB_REF_UNIFORM):
         lib = load()
         self.mesh = mesh          # keeps the mesh alive
-        self.p = make_params(params, precision, coef_mode, stream)
+        self.p = make_params(params, precision, coef_mode, stream, reference)
         rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
         u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
         if rho.size != mesh.ncell or u.size != mesh.ncell * mesh.dim:
