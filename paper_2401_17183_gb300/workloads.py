@@ -123,6 +123,20 @@ def channel_mesh(n0=256, n1=256, n2=256, stretch=2.5, bump=0.05, wall_links=0):
                  shift=[[n0, 0, 0], [0, 0, 0], [0, 0, n2]], wall_links=wall_links)
 
 
+def channel2d_mesh(n0=32, n1=16, stretch=0.7, wall_links=0):
+    """2D channel: axis 0 wall-normal with walls and tanh stretching (as in
+    channel_mesh), axis 1 streamwise, periodic and fastest in memory. The
+    geometry does not vary along axis 1."""
+    h = 0.5 * n0
+    s = 2.0 * (np.arange(n0, dtype=np.float64) + 0.5) / n0 - 1.0
+    ys = h * np.tanh(stretch * s) / math.tanh(stretch) if stretch > 0 else h * s
+    X = np.empty((n0, n1, 2))
+    X[..., 0] = ys[:, None]
+    X[..., 1] = np.arange(n1, dtype=np.float64)[None, :]
+    return _mesh(2, (n0, n1, 1), X, (WALL, PERIODIC), shift=[[0, 0, 0], [0, n1, 0]],
+                 wall_links=wall_links)
+
+
 def polar_mesh(nr, ntheta, r_in, r_out, dtheta=None, wall_links=0):
     """2D annular sector: r_i = r_in + (i + 1/2) dr (walls at r_in, r_out),
     theta_j = j dtheta, periodic in theta through a rotation by ntheta dtheta."""

