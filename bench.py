@@ -15,6 +15,7 @@ the fraction of the measured HBM copy bandwidth that the algorithmic traffic
 update) reaches.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--storage f32|f16|bf16 --reference rest|uniform]
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the workload,
 no collective on the data path (weak scaling); timing is the max over ranks.
@@ -34,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_CELL = {("19", "f32"): 2 * 19 * 4, ("19", "f64"): 2 * 19 * 8, ("9", "f32"): 2 * 9 * 4,
-                  ("9", "f64"): 2 * 9 * 8}
+                  ("9", "f64"): 2 * 9 * 8, ("19", "f16"): 2 * 19 * 2, ("19", "bf16"): 2 * 19 * 2}
 STEP_SOURCES = ["vlb_step.cu", "vlb_step.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_internal.cuh"]
 
 
@@ -49,6 +50,10 @@ def args_parse():
     ap.add_argument("--bump", type=float, default=0.05)
     ap.add_argument("--tau", type=float, default=0.8)
     ap.add_argument("--coef-mode", default="auto", choices=["auto", "full", "plane"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage (arithmetic stays FP32)")
+    ap.add_argument("--reference", default="rest", choices=["uniform", "rest"],
+                    help="storage reference of 16-bit populations")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -226,10 +231,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     metric = "MLUPS & % HBM roofline (fused D3Q19 stream-and-collide step)"
-    cfg = {"workload": "channel_d3q19_%d^3_fp32" % a.n, "cells": a.n ** 3, "lattice": "D3Q19",
+    cfg = {"workload": "channel_d3q19_%d^3_%s" % (a.n, "fp32" if a.storage == "f32" else a.storage),
+           "cells": a.n ** 3, "lattice": "D3Q19",
            "stretch": a.stretch, "bump": a.bump, "tau": a.tau, "walls": "eta (halfway bounce-back)",
            "periodic": "xi, zeta", "body_force": 1e-6,
-           "l2": "no flush: populations %.2f GB > 129 MB L2" % (a.n ** 3 * 152 / 2 / 1e9)}
+           "l2": "no flush: populations %.2f GB > 129 MB L2"
+                 % (a.n ** 3 * BYTES_PER_CELL[("19", a.storage)] / 2 / 1e9)}
+    if a.storage != "f32":
+        cfg["storage_reference"] = a.reference
 
     if a.impl == "reference":
         if rank != 0:
@@ -270,8 +279,10 @@ def main():
     gmesh = vlb.Mesh(mesh)
     info = gmesh.info()
     mode = {"auto": vlb.VLB_COEF_AUTO, "full": vlb.VLB_COEF_FULL, "plane": vlb.VLB_COEF_PLANE}[a.coef_mode]
-    sim = vlb.Sim(gmesh, prm, rho, u, precision=vlb.VLB_F32, coef_mode=mode,
-                  stream=stream.cuda_stream)
+    prec = {"f32": vlb.VLB_F32, "f16": vlb.VLB_F16, "bf16": vlb.VLB_BF16}[a.storage]
+    ref = vlb.VLB_REF_REST if a.reference == "rest" else vlb.VLB_REF_UNIFORM
+    sim = vlb.Sim(gmesh, prm, rho, u, precision=prec, coef_mode=mode, stream=stream.cuda_stream,
+                  reference=ref)
     lay = sim.layout()
     cfg["coef_mode"] = "plane" if lay["plane"] else "full"
     cfg["feq_rest_min"] = info["feq_rest_min"]
@@ -298,10 +309,10 @@ def main():
     ms = max_over_ranks(ms, dev)
     value = job_mlups(world, ncell, a.steps, ms / 1e3)
     per_launch_s = ms / 1e3 / a.steps
-    bpc = BYTES_PER_CELL[("19", "f32")]
+    bpc = BYTES_PER_CELL[("19", a.storage)]
     peak, peak_kind = measured_peak_hbm()
     achieved = bpc * ncell / per_launch_s / 1e9
-    traffic = ncu_traffic(ncell)
+    traffic = ncu_traffic(ncell) if a.storage == "f32" else None
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -334,12 +345,15 @@ def main():
     line = {
         "metric": metric, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.storage == "f32" else "%s storage, f32 arithmetic" % a.storage,
         "data": "synthetic (seeded mesh and 1% velocity noise)", "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_cell_update": bpc, "kernel": "k_step<19,float,float>",
+                     "bytes_per_cell_update": bpc,
+                     "kernel": "k_step<19,%s,float>" % {"f32": "float", "f16": "__half",
+                                                        "bf16": "__nv_bfloat16"}[a.storage],
                      "source_sha": source_sha()},
         "clocks": clocks, "e2e": e2e, "gpu_launches": a.steps, "cpu_baseline": cpu,
     }
