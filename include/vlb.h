@@ -204,6 +204,32 @@ int vlb_sim_layout(const vlb_sim *sim, int32_t *coef_per_cell, int32_t *plane_mo
 void vlb_destroy(vlb_sim *sim);
 const char *vlb_last_error(void);
 
+/* ---- Batches: many simulations advanced by one kernel launch per time step.
+ * Each member's time step is the same fused stream-and-collide of Eq. 12 /
+ * Eq. 22 as vlb_step (the per-cell arithmetic is identical, so a batch gives
+ * bit-for-bit the populations of stepping each member alone). The members'
+ * tiles (128 cells along the fastest axis) are cut into runs and every run is
+ * one block of a single launch; a member's work thus never waits for a launch
+ * of its own, which is what pays for many small meshes.
+ *   sims    nsims >= 1 simulations on the current device with the same
+ *           lattice, precision (VLB_F32 or VLB_F64), coefficient mode (all
+ *           plane or all full), time parity and stream, each with fewer than
+ *           2^31 / q cells; they must outlive the batch and are not copied
+ * Errors: VLB_EINVAL (mismatch, 16-bit storage, NULL), VLB_ENOMEM, VLB_ECUDA. */
+typedef struct vlb_batch vlb_batch;
+int vlb_batch_create(vlb_sim *const *sims, int32_t nsims, vlb_batch **out);
+/* Advance every member nsteps steps (asynchronous on the members' stream;
+ * errors raised by kernels are sticky per member, see vlb_sync). Whole runs
+ * of 32 steps replay a CUDA graph of 32 launches built on first use. */
+int vlb_batch_step(vlb_batch *b, int64_t nsteps);
+/* Pick the run length (tiles per block) by timing: each of a few candidates
+ * runs `steps` steps on the members (the simulations advance by
+ * 4 * steps in total). Blocks until done. run_length_out may be NULL. */
+int vlb_batch_tune(vlb_batch *b, int32_t steps, int64_t *run_length_out);
+/* Blocks (tile runs) per launch and tiles per run; for reporting. */
+int vlb_batch_layout(const vlb_batch *b, int64_t *blocks, int64_t *run_length, int64_t *cells);
+void vlb_batch_destroy(vlb_batch *b);
+
 /* The paper has no counterpart to this call: it is a service for callers that
  * cannot allocate device memory -- code whose device memory comes from a fixed
  * budget or from a pool allocator it does not own, and latency-bound

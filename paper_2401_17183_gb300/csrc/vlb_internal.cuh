@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/vlb.h"
 
 namespace vlb {
@@ -395,6 +397,20 @@ struct vlb_sim {
   int64_t partial_blocks = 0;
   double *d_io = nullptr;     // host<->device staging for init/state, grown on demand
   size_t io_bytes = 0;
+};
+
+struct vlb_batch {
+  std::vector<vlb_sim *> sims;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t run = 0;            // tiles per block
+  int64_t nitems = 0;         // blocks per launch
+  int64_t cells = 0;
+  void *d_args = nullptr;     // StepArgs[nsims]
+  void *d_items = nullptr;    // BatchItem[nitems]
+  size_t items_cap = 0;
+  cudaGraphExec_t graph = nullptr;  // 32 launches, even parity first
+  int64_t graph_run = 0;      // run length the graph was built for
 };
 
 namespace vlb {

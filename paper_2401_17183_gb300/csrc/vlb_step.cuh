@@ -145,8 +145,9 @@ __device__ __forceinline__ __nv_bfloat16 s16_from_bits<__nv_bfloat16>(unsigned s
 
 // REFOFS: 16-bit populations stored relative to the local rest state (the
 // offsets from the uniform reference come with the record, plane mode only).
+// The tiles [t0, t1) of one mesh, as one block.
 template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, typename IT>
-__global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(const StepArgs a) {
+__device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, const int64_t t1) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
   constexpr int RS = L::template stride<R>();
@@ -157,9 +158,6 @@ __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(con
   static_assert(RCHUNK <= kStepThreads, "record larger than one copy per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<Q, S, R> &sm = *reinterpret_cast<StepSmem<Q, S, R> *>(smem_raw);
-  const int64_t t0 = (int64_t)blockIdx.x * a.per_block;
-  const int64_t t1 = t0 + a.per_block < a.ntiles ? t0 + a.per_block : a.ntiles;
-  if (t0 >= t1) return;
   S *__restrict__ f = static_cast<S *>(a.f);
   const R *__restrict__ coef = static_cast<const R *>(a.coef);
   const IT ps = (IT)a.ncell;
@@ -296,27 +294,34 @@ __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>()) k_step(con
   cp_async_wait<0>();
 }
 
-// blocks the persistent kernel can keep resident on the current device
-// (queried once per kernel and device)
-static int resident_blocks(const void *kern, size_t smem) {
-  static std::mutex mu;
-  static std::vector<std::tuple<const void *, int, int>> cache;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lock(mu);
-  for (const auto &e : cache)
-    if (std::get<0>(e) == kern && std::get<1>(e) == dev) return std::get<2>(e);
-  int nb = 0, nsm = 0;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStepThreads, smem);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int total = (nb > 0 ? nb : 1) * (nsm > 0 ? nsm : 1);
-  cache.emplace_back(kern, dev, total);
-  return total;
+// One mesh: block b walks the tiles [b per_block, (b + 1) per_block).
+template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, typename IT>
+__global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>())
+    k_step(const __grid_constant__ StepArgs a) {
+  const int64_t t0 = (int64_t)blockIdx.x * a.per_block;
+  const int64_t t1 = t0 + a.per_block < a.ntiles ? t0 + a.per_block : a.ntiles;
+  if (t0 >= t1) return;
+  step_tiles<Q, S, R, ODD, PLANE, REFOFS, IT>(a, t0, t1);
 }
 
-template <int Q, typename S, typename R>
-cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
+// Many meshes in one launch: block b takes the run of tiles items[b] of mesh
+// items[b].sim, whose arguments are args[items[b].sim].
+struct BatchItem {
+  int32_t sim;
+  int32_t pad;
+  int64_t t0, t1;
+};
+
+template <int Q, typename S, typename R, bool ODD, bool PLANE, typename IT>
+__global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>())
+    k_step_batch(const StepArgs *__restrict__ args, const BatchItem *__restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  step_tiles<Q, S, R, ODD, PLANE, false, IT>(args[it.sim], it.t0, it.t1);
+}
+
+// Arguments of one simulation's step kernel (per_block left for the caller).
+template <int Q>
+inline StepArgs make_step_args(const vlb_sim *sim) {
   const vlb_mesh *m = sim->mesh;
   StepArgs a;
   a.f = sim->d_f;
@@ -340,6 +345,33 @@ cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
   a.nA = (int32_t)(dim == 3 ? m->md.n[0] : 1);
   a.nB = (int32_t)(dim == 3 ? m->md.n[1] : m->md.n[0]);
   a.ntiles = (int64_t)a.ntf * a.nA * a.nB;
+  a.per_block = 0;
+  return a;
+}
+
+// blocks the persistent kernel can keep resident on the current device
+// (queried once per kernel and device)
+static int resident_blocks(const void *kern, size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::tuple<const void *, int, int>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto &e : cache)
+    if (std::get<0>(e) == kern && std::get<1>(e) == dev) return std::get<2>(e);
+  int nb = 0, nsm = 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStepThreads, smem);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int total = (nb > 0 ? nb : 1) * (nsm > 0 ? nsm : 1);
+  cache.emplace_back(kern, dev, total);
+  return total;
+}
+
+template <int Q, typename S, typename R>
+cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
+  const vlb_mesh *m = sim->mesh;
+  StepArgs a = make_step_args<Q>(sim);
   // 32-bit indexing when every population offset fits
   const bool i32 = (int64_t)Q * m->ncell < ((int64_t)1 << 31);
   if (a.ntiles == 0) return cudaSuccess;

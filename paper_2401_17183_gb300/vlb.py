@@ -82,6 +82,12 @@ def load():
         "vlb_destroy": ([vp], None),
         "vlb_last_error": ([], C.c_char_p),
         "vlb_totals_noalloc": ([vp, vp], C.c_int),
+        "vlb_batch_create": ([C.POINTER(vp), C.c_int32, C.POINTER(vp)], C.c_int),
+        "vlb_batch_step": ([vp, C.c_int64], C.c_int),
+        "vlb_batch_tune": ([vp, C.c_int32, C.POINTER(C.c_int64)], C.c_int),
+        "vlb_batch_layout": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int64)], C.c_int),
+        "vlb_batch_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -262,6 +268,43 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             load().vlb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """vlb_batch_create / vlb_batch_step / vlb_batch_tune / vlb_batch_destroy:
+    many simulations advanced by one kernel launch per time step."""
+
+    def __init__(self, sims):
+        lib = load()
+        self.sims = list(sims)    # keeps the members alive
+        arr = (C.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        h = C.c_void_p()
+        _check(lib.vlb_batch_create(arr, len(self.sims), C.byref(h)), "vlb_batch_create")
+        self.h = h
+
+    def step(self, n=1):
+        _check(load().vlb_batch_step(self.h, int(n)), "vlb_batch_step")
+
+    def tune(self, steps=10):
+        r = C.c_int64()
+        _check(load().vlb_batch_tune(self.h, int(steps), C.byref(r)), "vlb_batch_tune")
+        return r.value
+
+    def layout(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().vlb_batch_layout(self.h, C.byref(a), C.byref(b), C.byref(c)), "vlb_batch_layout")
+        return {"blocks": a.value, "run_length": b.value, "cells": c.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().vlb_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
