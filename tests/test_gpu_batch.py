@@ -36,7 +36,7 @@ def _channels(V, prec=None):
 
 def _d2q9_full(V):
     meshes = [W.periodic_sine_mesh(16, 0.02), W.periodic_sine_mesh(40, 0.02),
-              W.polar_mesh(16, 3, 30.0, 36.0, dtheta=1.0 / 33), W.periodic_sine_mesh(24, 0.01)]
+              W.polar_mesh(16, 3, 300.0, 316.0, dtheta=1.0 / 308), W.periodic_sine_mesh(24, 0.01)]
     sims = []
     for i, mesh in enumerate(meshes):
         rho, u = W.noise_fields(mesh, amp=0.005, seed=20 + i)
