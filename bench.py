@@ -16,6 +16,7 @@ update) reaches.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
                   [--storage f32|f16|bf16 --reference rest|uniform]
+                  [--workload batch --nmesh M]   (M uneven D2Q9 meshes, one launch per step)
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the workload,
 no collective on the data path (weak scaling); timing is the max over ranks.
@@ -56,6 +57,9 @@ def args_parse():
                     help="storage reference of 16-bit populations")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="channel", choices=["channel", "batch"],
+                    help="batch: many uneven D2Q9 meshes advanced by one launch per step")
+    ap.add_argument("--nmesh", type=int, default=512)
     return ap.parse_args()
 
 
@@ -225,8 +229,91 @@ def cpu_baseline_leg(tau, stretch, bump):
                       % (stretch, bump, tau, k, el)}
 
 
+def batch_meshes(nmesh, seed=4):
+    """Seeded uneven 2D channels: streamwise (periodic, fastest) size
+    log-uniform in [64, 512], wall-normal size half of it, tanh stretching
+    uniform in [0.3, 0.9]."""
+    import numpy as np
+    from paper_2401_17183_gb300 import workloads as W
+    u = W.uniform(seed, nmesh, 2)
+    out = []
+    for k in range(nmesh):
+        n1 = int(round(64 * 8 ** u[k, 0]))
+        n0 = max(4, n1 // 2)
+        out.append(W.channel2d_mesh(n0, n1, stretch=0.3 + 0.6 * u[k, 1]))
+    return out
+
+
+def bench_batch(a):
+    """One kernel launch per time step for the whole set (CUDA graph replays),
+    against stepping every mesh on its own."""
+    import numpy as np
+    import torch
+
+    from paper_2401_17183_gb300 import build as B
+    B.build()
+    from paper_2401_17183_gb300 import vlb
+    from paper_2401_17183_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    meshes = batch_meshes(a.nmesh)
+    sims = []
+    for k, mesh in enumerate(meshes):
+        rho, u = W.noise_fields(mesh, amp=0.01, seed=100 + k)
+        sims.append(vlb.Sim(vlb.Mesh(mesh), W.params(a.tau, body_force=(0.0, 1e-6, 0.0)), rho, u,
+                            precision=vlb.VLB_F32, stream=stream.cuda_stream))
+    ncell = sum(W.ncell(m) for m in meshes)
+    batch = vlb.Batch(sims)
+    run = batch.tune(4)
+    batch.step(a.warmup)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    ms = timed(lambda: batch.step(a.steps))
+    clocks = sampler.stop()
+    for s in sims:
+        s.sync()
+    k_alone = max(2, a.steps // 10)
+    ms_alone = timed(lambda: [s.step(k_alone) for s in sims])
+    for s in sims:
+        s.sync()
+    value = ncell * a.steps / (ms / 1e3) / 1e6
+    alone = ncell * k_alone / (ms_alone / 1e3) / 1e6
+    bpc = BYTES_PER_CELL[("9", "f32")]
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bpc * ncell / (ms / 1e3 / a.steps) / 1e9
+    lay = batch.layout()
+    line = {
+        "metric": "MLUPS, batch of uneven D2Q9 meshes in one launch per step", "value": value,
+        "unit": "MLUPS", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded meshes and 1% velocity noise)",
+        "config": {"workload": "batch_%d_channel2d_d2q9_fp32" % a.nmesh, "meshes": a.nmesh, "cells": ncell,
+                   "sizes": "streamwise log-uniform 64..512, wall-normal half", "tau": a.tau,
+                   "blocks_per_launch": lay["blocks"], "tiles_per_block": run,
+                   "graph": "32 launches per CUDA graph"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "bytes_per_cell_update": bpc},
+        "one_launch_per_mesh": {"value": alone, "unit": "MLUPS", "steps": k_alone,
+                                "speedup_of_batch": value / alone},
+        "clocks": clocks, "gpu_launches": a.steps,
+    }
+    print(json.dumps(line))
+
+
 def main():
     a = args_parse()
+    if a.workload == "batch":
+        return bench_batch(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
