@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
 SOURCES = ["vlb_api.cu", "vlb_geometry.cu", "vlb_step.cu", "vlb_step16.cu", "vlb_batch.cu",
-           "vlb_moments.cu", "vlb_noalloc.cu"]
+           "vlb_moments.cu", "vlb_noalloc.cu", "vlb_nn.cu"]
 HEADERS = ["vlb_internal.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_step.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -41,7 +41,8 @@ def _stale(target, deps):
 
 def _inc_deps():
     return [os.path.join(CSRC, h) for h in HEADERS] + [
-        os.path.join(HERE, "..", "include", "vlb.h"), os.path.abspath(__file__)]
+        os.path.join(HERE, "..", "include", "vlb.h"), os.path.join(HERE, "..", "include", "vlb_nn.h"),
+        os.path.abspath(__file__)]
 
 
 def _compile(src, verbose):
