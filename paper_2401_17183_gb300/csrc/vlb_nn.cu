@@ -266,7 +266,17 @@ __global__ void k_convert(const float *__restrict__ in, TO *__restrict__ out, in
   if (i < n) out[i] = st<TO>(in[i]);
 }
 
-// out[b][c][p] = in[b][c][p] for a channel block (copy between views)
+// dst[b][r] = src[b][r] (converted) for r < CHW: the input into its view
+template <typename TO>
+__global__ void k_convert_into(const float *__restrict__ src, int64_t sbs, TO *__restrict__ dst, int64_t dbs,
+                               int64_t CHW, int B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= CHW * B) return;
+  const int64_t b = i / CHW, r = i % CHW;
+  dst[b * dbs + r] = st<TO>(src[b * sbs + r]);
+}
+
+// dst[b][r] += src[b][r] for a channel block (between views)
 __global__ void k_add_into(const float *__restrict__ src, int64_t sbs, float *__restrict__ dst, int64_t dbs, int64_t CHW,
                            int B) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,8 +472,8 @@ int forward_t(vlb_nn *n, const float *d_x, float *d_y, int B) {
   const int w = n->width, H = n->H, W = n->W, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
   const auto &L = n->L;
   // input in the storage type
-  const int64_t nx = (int64_t)B * n->ci * H * W;
-  nn::k_convert<T><<<nn::nblk(nx), 256>>>(d_x, A + n->x_in.off, nx);
+  const int64_t chw = (int64_t)n->ci * H * W;
+  nn::k_convert_into<T><<<nn::nblk(chw * B), 256>>>(d_x, chw, A + n->x_in.off, n->x_in.bs, chw, B);
   NN_CU(cudaGetLastError());
   NN_TRY(conv<T>(n, L[0], A + n->x_in.off, n->x_in.bs, wp(L[0]), n->p + L[0].boff, A + n->e1.off, n->e1.bs, true, false, B));
   NN_TRY(conv<T>(n, L[1], A + n->e1.off, n->e1.bs, wp(L[1]), n->p + L[1].boff, A + n->s1.off, n->s1.bs, true, false, B));

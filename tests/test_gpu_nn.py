@@ -105,4 +105,4 @@ def test_training_reduces_loss(NN):
         losses.append(net.mse(dy.data_ptr(), target.data_ptr(), ddy.data_ptr(), B))
         net.backward(ddy.data_ptr(), B)
         net.adam(3e-3, it)
-    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+    assert losses[-1] < 0.25 * losses[0], (losses[0], losses[-1])
