@@ -123,16 +123,20 @@ def channel_mesh(n0=256, n1=256, n2=256, stretch=2.5, bump=0.05, wall_links=0):
                  shift=[[n0, 0, 0], [0, 0, 0], [0, 0, n2]], wall_links=wall_links)
 
 
-def channel2d_mesh(n0=32, n1=16, stretch=0.7, wall_links=0):
+def channel2d_mesh(n0=32, n1=16, stretch=0.7, wall_links=0, bump=0.0):
     """2D channel: axis 0 wall-normal with walls and tanh stretching (as in
-    channel_mesh), axis 1 streamwise, periodic and fastest in memory. The
-    geometry does not vary along axis 1."""
+    channel_mesh), axis 1 streamwise, periodic and fastest in memory. Without
+    a bump the geometry does not vary along axis 1; bump (a fraction of the
+    half height h) raises the lower wall by bump h sin(2 pi x / n1), blended
+    out linearly toward the upper wall."""
     h = 0.5 * n0
     s = 2.0 * (np.arange(n0, dtype=np.float64) + 0.5) / n0 - 1.0
     ys = h * np.tanh(stretch * s) / math.tanh(stretch) if stretch > 0 else h * s
+    xs = np.arange(n1, dtype=np.float64)
+    bl = bump * h * np.sin(2 * np.pi * xs / n1)
     X = np.empty((n0, n1, 2))
-    X[..., 0] = ys[:, None]
-    X[..., 1] = np.arange(n1, dtype=np.float64)[None, :]
+    X[..., 0] = ys[:, None] + bl[None, :] * (1.0 - ys[:, None] / h) / 2.0
+    X[..., 1] = xs[None, :]
     return _mesh(2, (n0, n1, 1), X, (WALL, PERIODIC), shift=[[0, 0, 0], [0, n1, 0]],
                  wall_links=wall_links)
 
