@@ -17,6 +17,7 @@ update) reaches.
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
                   [--storage f32|f16|bf16 --reference rest|uniform]
                   [--workload batch --nmesh M]   (M uneven D2Q9 meshes, one launch per step)
+                  [--workload warmstart --ntrain N --ntest M --iters K]   (learned warm start)
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the workload,
 no collective on the data path (weak scaling); timing is the max over ranks.
@@ -57,8 +58,12 @@ def args_parse():
                     help="storage reference of 16-bit populations")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="channel", choices=["channel", "batch"],
-                    help="batch: many uneven D2Q9 meshes advanced by one launch per step")
+    ap.add_argument("--workload", default="channel", choices=["channel", "batch", "warmstart"],
+                    help="batch: many uneven D2Q9 meshes advanced by one launch per step; "
+                         "warmstart: train the warm-start network and compare time to steady")
+    ap.add_argument("--ntrain", type=int, default=2048)
+    ap.add_argument("--ntest", type=int, default=256)
+    ap.add_argument("--iters", type=int, default=3000)
     ap.add_argument("--nmesh", type=int, default=512)
     return ap.parse_args()
 
@@ -310,10 +315,56 @@ def bench_batch(a):
     print(json.dumps(line))
 
 
+def bench_warmstart(a):
+    """Steps and wall time to a 1e-6 residual from the learned prediction and
+    from rest, on held-out members of the bumped 2D channel family."""
+    import numpy as np
+
+    from paper_2401_17183_gb300 import build as B
+    B.build()
+    from paper_2401_17183_gb300 import warmstart as WS
+    t0 = time.perf_counter()
+    X, Y, keep = WS.dataset(WS.family(4, a.ntrain))
+    t_data = time.perf_counter() - t0
+    ws = WS.WarmStart()
+    losses, t_train = ws.train(X, Y, a.iters)
+    test = WS.family(5, a.ntest)
+    Xt, Yt, kt = WS.dataset(test)
+    tspec = [test[k] for k in kt]
+    t1 = time.perf_counter()
+    pred = ws.predict(Xt)
+    t_pred = time.perf_counter() - t1
+    err = [float(np.linalg.norm(np.stack([p[1][..., 0], p[1][..., 1]]) - Yt[i, 1:]) / np.linalg.norm(Yt[i, 1:]))
+           for i, p in enumerate(pred)]
+    cold = [m[2] for m in WS.make_sims(tspec)]
+    sc, tc = WS.run_to_steady(cold)
+    warm = [m[2] for m in WS.make_sims(tspec, init=pred)]
+    sw, tw = WS.run_to_steady(warm)
+    line = {
+        "metric": "time-to-steady (1e-6 residual), learned warm start vs plain cold start",
+        "value": float(sc.mean() / sw.mean()), "unit": "x fewer steps (mean over held-out members)",
+        "n_gpus": 1, "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 solver; bf16 network storage with f32 accumulation",
+        "data": "synthetic (seeded bumped 2D channels; steady targets from the solver)",
+        "config": {"workload": "warmstart_channel2d_32x64_d2q9", "train_members": len(keep),
+                   "test_members": len(kt), "iters": a.iters, "batch": ws.batch,
+                   "params": ws.net.nparams, "tau": WS.TAU},
+        "cold": {"steps_mean": float(sc.mean()), "steps_max": int(sc.max()), "wall_s": tc},
+        "warm": {"steps_mean": float(sw.mean()), "steps_max": int(sw.max()), "wall_s": tw + t_pred,
+                 "inference_s": t_pred},
+        "prediction_u_rel_err": {"mean": float(np.mean(err)), "max": float(np.max(err))},
+        "train": {"loss_first": losses[0], "loss_last": losses[-1], "seconds": t_train,
+                  "data_seconds": t_data},
+    }
+    print(json.dumps(line))
+
+
 def main():
     a = args_parse()
     if a.workload == "batch":
         return bench_batch(a)
+    if a.workload == "warmstart":
+        return bench_warmstart(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
