@@ -15,7 +15,8 @@
 // Directions come in pairs (p, pbar = p + H) with c_pbar = -c_p; every sum over
 // directions is a sum over pairs of an even part (same for p and pbar) and an
 // odd part (opposite signs), with the link coefficients stored as
-// M_p = K_p + K_pbar and D_p = K_p - K_pbar.
+// M_p = K_p + K_pbar and D_p = K_p - K_pbar (stored with the weights they
+// carry in the constant part of the map).
 //
 // The map Phi -> Phi_new of Eq. 27 is evaluated in a reduced form. Writing
 //   N'_a - w_a n_ref = (1 - 1/tau) d_a + w_a (mdev + m x_a)/tau + deltaN_a,
@@ -113,8 +114,9 @@ __device__ void build_record(double J, const double *ginv, const double *G,
       M[p][i] = K[p][i] + K[p + H][i];
       Dk[p][i] = K[p][i] - K[p + H][i];
       c[p][i] = Lat<Q>::c(p, i);
-      rec[L::mp(p, i)] = M[p][i];
-      rec[L::dk(p, i)] = Dk[p][i];
+      // stored with the weights they carry in the constant part of the map
+      rec[L::mp(p, i)] = -0.25 * (2.0 - itau) * M[p][i];
+      rec[L::dk(p, i)] = 0.25 * itau * Dk[p][i];
     }
   }
   double Rt[D][D][D];
@@ -215,8 +217,9 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
   }
   // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a - L^j_a) f^eq_a   (Eq. 30):
   // K_a - L_a = K_a + K_abar = M_p, and a pair contributes c_p (f_p - f_pbar)
-  // with f_p - f_pbar = 2 rho w_p xo_p
-  const R cpr = -(R(1) - R(0.5) * itau) * rho;
+  // with f_p - f_pbar = 2 rho w_p xo_p. The record holds am M_p with
+  // am = -(2 - 1/tau)/4, and -1/2 (1 - 1/(2 tau)) 2 rho = 2 rho am.
+  const R r2 = R(2) * rho;
   R dP[D][D];
 #pragma unroll
   for (int i = 0; i < D; i++)
@@ -224,15 +227,15 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
     for (int j = 0; j < D; j++) dP[i][j] = R(0);
 #pragma unroll
   for (int p = 1; p <= H; p++) {
-    const R df = cpr * lat_w<Q, R>(p) * xo[p];
+    const R df = r2 * lat_w<Q, R>(p) * xo[p];
 #pragma unroll
     for (int j = 0; j < D; j++) {
-      const R t = rc[L::mp(p, j)] * df;
+      const R amM = rc[L::mp(p, j)];
 #pragma unroll
       for (int i = 0; i < D; i++) {
         const int ci = Lat<Q>::c(p, i);
-        if (ci > 0) dP[i][j] += t;
-        if (ci < 0) dP[i][j] -= t;
+        if (ci > 0) dP[i][j] = fmar(amM, df, dP[i][j]);
+        if (ci < 0) dP[i][j] = fmar(-amM, df, dP[i][j]);
       }
     }
   }
@@ -323,9 +326,9 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
   // the parts of -1/2 sum_a K_a N'_a that do not change during the iteration
   // and the terms of the map that depend on U only. Over a pair,
   //   -1/2 (K_pbar d_p + K_p d_pbar) - 1/2 (1 - 1/tau)(K_p d_p + K_pbar d_pbar)
-  //     = -(2 - 1/tau)/4 M_p s_p + (1/tau)/4 D_p t_p.
+  //     = -(2 - 1/tau)/4 M_p s_p + (1/tau)/4 D_p t_p,
+  // whose two weights the record's link coefficients already carry.
   R Pb[D];
-  const R am = -R(0.25) * (R(2) - itau), ad = R(0.25) * itau;
 #pragma unroll
   for (int i = 0; i < D; i++) {
     const R kw = rc[L::KW + i];
@@ -334,7 +337,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     R s = m * rc[L::BODY + i] - err - R(0.5) * itau * mdev * kw;
 #pragma unroll
     for (int p = 1; p <= H; p++)
-      s += am * rc[L::mp(p, i)] * sp[p] + ad * rc[L::dk(p, i)] * tp[p];
+      s = fmar(rc[L::dk(p, i)], tp[p], fmar(rc[L::mp(p, i)], sp[p], s));
     R u = rc[L::CE + i];
 #pragma unroll
     for (int l = 0; l < D; l++) u += rc[L::PO1 + i * D + l] * st.U[l];

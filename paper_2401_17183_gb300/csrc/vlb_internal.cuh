@@ -90,7 +90,9 @@ __host__ __device__ constexpr int offd(int k, int l) {
 // coefficients, and the coefficients of one evaluation of the map.
 //
 // Link coefficients are stored per pair (p, pbar = p + H) as
-// M_p = K_p + K_pbar and D_p = K_p - K_pbar, interleaved pair by pair. The
+// am M_p and ad D_p with M_p = K_p + K_pbar, D_p = K_p - K_pbar and the weights
+// am = -(2 - 1/tau)/4, ad = (1/tau)/4 that they carry in the constant part
+// of the map (see collide_cell), interleaved pair by pair. The
 // last group holds the coefficients of the fixed-point map of Eq. 27 written
 // as a polynomial in U~ (see build_record), so that one evaluation of the map
 // costs a few dozen products instead of a pass over all directions.
@@ -111,7 +113,7 @@ struct CoefLayout {
   static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
   static constexpr int CE = UW + D;            // constant term of the map
   static constexpr int PO1 = CE + D;           // D x D: coefficient of U
-  // link coefficients: M_p^i at MPD + (p-1)*2D + i, D_p^i at MPD + (p-1)*2D + D + i
+  // link coefficients: am M_p^i at MPD + (p-1)*2D + i, ad D_p^i at MPD + (p-1)*2D + D + i
   static constexpr int MPD = round4(PO1 + D * D);
   // one evaluation of the map
   static constexpr int HM = round4(MPD + 2 * H * D);  // D x D chord matrix (I - L)^-1
@@ -146,6 +148,8 @@ __device__ __forceinline__ R maxnan(R a, R b) {
   return (a > b || a != a) ? a : b;
 }
 __device__ __forceinline__ float absr(float x) { return fabsf(x); }
+__device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ double absr(double x) { return fabs(x); }
 
 // population storage types: FP64, FP32, IEEE half, bfloat16
