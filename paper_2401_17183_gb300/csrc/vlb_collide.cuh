@@ -96,6 +96,7 @@ __device__ void build_record(double J, const double *ginv, const double *G,
   const double T0 = kT0, itau = 1.0 / tau, cpi = -(1.0 - 0.5 * itau);
   for (int k = 0; k < L::NC; k++) rec[k] = 0.0;
   rec[L::J] = J;
+  rec[L::IJ] = 1.0 / J;
   double gd[D][D];
   for (int i = 0; i < D; i++)
     for (int j = 0; j < D; j++) gd[i][j] = ginv[sym<D>(i, j)] - (i == j ? 1.0 : 0.0);
@@ -196,14 +197,13 @@ __device__ __forceinline__ double two_prod_err(double x, double y, double p) { r
 // relative to itself and not to the much larger d_a.
 template <int Q, typename R>
 __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ rc, R m, R mdev,
-                                        R rho, R itau, const R (&U)[Lat<Q>::D],
+                                        R h2m, R rho, R itau, const R (&U)[Lat<Q>::D],
                                         const R (&Phi)[Lat<Q>::D], R (&dp)[Q]) {
   using L = CoefLayout<Q>;
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   R gd[L::NS], dU[D];
 #pragma unroll
   for (int i = 0; i < L::NS; i++) gd[i] = rc[L::GINV + i];
-  const R h2m = R(0.5) / m;
 #pragma unroll
   for (int i = 0; i < D; i++) dU[i] = Phi[i] * h2m;
   EqParts<Q, R> e;
@@ -285,10 +285,11 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
 // is the unit roundoff of R, and Phi is a sum of dozens of rounded terms of
 // its own size, so smaller corrections are rounding noise. With FINAL, the
 // post-collision deviations are formed at the converged Phi.
-// rc points at the cell's coefficient record (global or local memory).
+// rc points at the cell's coefficient record (global, shared or local
+// memory); itau = 1/tau.
 template <int Q, typename R, bool CHORD, bool FINAL>
 __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restrict__ rc, R nref,
-                                             R tau, R tol, int max_iter, R (&dp)[Q],
+                                             R itau, R tol, int max_iter, R (&dp)[Q],
                                              CollideState<Q, R> &st) {
   using L = CoefLayout<Q>;
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H, NS = L::NS;
@@ -303,9 +304,8 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     mdev += sp[p];
   }
   const R m = nref + mdev;
-  const R J = rc[L::J];
   // rho = sum f = sum N / J; rho U = sum c f   (Eqs. 14, 15, 17)
-  st.rho = m / J;
+  st.rho = m * rc[L::IJ];
   const R im = R(1) / m;
   const R h2m = R(0.5) * im;
 #pragma unroll
@@ -319,7 +319,6 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     }
     st.U[i] = s * im;
   }
-  const R itau = R(1) / tau;
   // constant part of J F: body force m G, 1/2 sum_a L_a N_a (L_a = -K_abar), the
   // reference part -n_ref sum_a w_a K_a of both sums of Eq. 27 (the largest term,
   // the same every step: formed without rounding error from the split KW + KWL),
@@ -406,10 +405,9 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     }
   }
   st.iters = it;
-  if (FINAL) form_np<Q, R>(d, rc, m, mdev, st.rho, itau, st.U, Phi, dp);
-  const R iJ = R(1) / J;
+  if (FINAL) form_np<Q, R>(d, rc, m, mdev, h2m, st.rho, itau, st.U, Phi, dp);
 #pragma unroll
-  for (int i = 0; i < D; i++) st.F[i] = Phi[i] * iJ;
+  for (int i = 0; i < D; i++) st.F[i] = Phi[i] * rc[L::IJ];
 }
 
 }  // namespace vlb

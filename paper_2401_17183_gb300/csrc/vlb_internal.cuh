@@ -113,8 +113,9 @@ struct CoefLayout {
   static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
   static constexpr int CE = UW + D;            // constant term of the map
   static constexpr int PO1 = CE + D;           // D x D: coefficient of U
+  static constexpr int IJ = PO1 + D * D;       // 1 / J
   // link coefficients: am M_p^i at MPD + (p-1)*2D + i, ad D_p^i at MPD + (p-1)*2D + D + i
-  static constexpr int MPD = round4(PO1 + D * D);
+  static constexpr int MPD = round4(IJ + 1);
   // one evaluation of the map
   static constexpr int HM = round4(MPD + 2 * H * D);  // D x D chord matrix (I - L)^-1
   static constexpr int PE = HM + D * D;        // D x NS: coefficient of U~^k U~^l (k <= l)

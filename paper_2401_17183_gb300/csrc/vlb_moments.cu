@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
     double Np[Q];
     CollideState<Q, double> st;
     // plain fixed point from F = 0 on the full populations (n_ref = 0)
-    collide_cell<Q, double, false, false>(N, rec, 0.0, a.tau, 1e-14, 200, Np, st);
+    collide_cell<Q, double, false, false>(N, rec, 0.0, 1.0 / a.tau, 1e-14, 200, Np, st);
     if (!st.conv) atomicOr(a.err, ERR_NOCONV);
     double gl[D][D];
     for (int i = 0; i < D; i++)

@@ -49,6 +49,10 @@ struct StepArgs {
   int32_t plane;    // one coefficient record per column of the fastest axis
   double tau, tol;
   double nref;      // populations are stored as N_a - w_a nref
+  double itau;      // 1 / tau
+  // the same scalars rounded once for FP32 arithmetic, so that no cell
+  // converts them
+  float nref_f, itau_f, tol_f;
   int32_t max_iter;
   int32_t moving;
   // tiles: index t = (A nB + B) ntf + tf over the two slow axes (A, B) and
@@ -73,6 +77,18 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// a step argument in the arithmetic type: the FP64 value or its FP32 copy
+template <typename R>
+__device__ __forceinline__ R arg_r(double v, float vf);
+template <>
+__device__ __forceinline__ double arg_r<double>(double v, float) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float arg_r<float>(double, float vf) {
+  return vf;
 }
 
 // position of a tile in the (A, B, tf) mixed radix
@@ -248,7 +264,8 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
       // ---- collide (section 2.2)
       R Np[Q];
       CollideState<Q, R> cst;
-      collide_cell<Q, R, true, true>(N, rc, R(a.nref), R(a.tau), R(a.tol), a.max_iter, Np, cst);
+      collide_cell<Q, R, true, true>(N, rc, arg_r<R>(a.nref, a.nref_f), arg_r<R>(a.itau, a.itau_f),
+                                     arg_r<R>(a.tol, a.tol_f), a.max_iter, Np, cst);
       if (!cst.conv) atomicOr(a.err, ERR_NOCONV);
 
       // ---- moving walls: a reflected population is corrected by
@@ -333,6 +350,10 @@ inline StepArgs make_step_args(const vlb_sim *sim) {
   a.tau = sim->p.tau;
   a.tol = sim->p.tol;
   a.nref = sim->nref;
+  a.itau = 1.0 / sim->p.tau;
+  a.nref_f = (float)a.nref;
+  a.itau_f = (float)a.itau;
+  a.tol_f = (float)a.tol;
   a.max_iter = sim->p.max_iter;
   a.moving = 0;
   for (int ax = 0; ax < 3; ax++)
