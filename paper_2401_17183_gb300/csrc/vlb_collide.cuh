@@ -206,20 +206,64 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
   for (int i = 0; i < L::NS; i++) gd[i] = rc[L::GINV + i];
 #pragma unroll
   for (int i = 0; i < D; i++) dU[i] = Phi[i] * h2m;
-  EqParts<Q, R> e;
-  eq_parts<Q, R>(gd, U, dU, e);
+  // The even and odd parts of the bracket of Eq. 33 divided by 3 (the factor
+  // moves into the per-weight constants below), from B and C^kkl of eq_parts
+  // scaled by 3/2 (with T0 = 1/3):
+  //   xe_p / 3 = c_p.Bh.c_p - tr Bh / 3,   Bh = (3/2) B,
+  //   xo_p / 3 = c_p.U + sum_{k != l} C2h^kl c^l_p (3 (c^k_p)^2 - 1),   C2h = (3/2) C^kkl.
+  const R hT0 = R(1.5 * kT0);
+  R Ut[D], Uh[D];
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    Ut[i] = U[i] + dU[i];
+    Uh[i] = R(1.5) * Ut[i];
+  }
+  R Bh[D][D], tB3 = R(0);
+#pragma unroll
+  for (int i = 0; i < D; i++)
+#pragma unroll
+    for (int j = i; j < D; j++) {
+      Bh[i][j] = gd[sym<D>(i, j)] * hT0 + Uh[i] * Ut[j];
+      Bh[j][i] = Bh[i][j];
+    }
+#pragma unroll
+  for (int i = 0; i < D; i++) tB3 += Bh[i][i];
+  tB3 *= R(1.0 / 3.0);
+  R C2h[D][D];
+#pragma unroll
+  for (int i = 0; i < D; i++)
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      if (i == j) continue;
+      C2h[i][j] = hT0 * ((gd[sym<D>(i, i)] * Ut[j] + dU[j]) + R(2) * gd[sym<D>(i, j)] * Ut[i]) +
+                  Uh[i] * Ut[i] * Ut[j];
+    }
   R xe[H + 1], xo[H + 1];
-  xe[0] = eq_even_dev<Q, R>(e, 0);
+  xe[0] = -tB3;
 #pragma unroll
   for (int p = 1; p <= H; p++) {
-    xe[p] = eq_even_dev<Q, R>(e, p);
-    xo[p] = eq_odd<Q, R>(e, U, p);
+    R cbc = R(0), x = R(0);
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const int ci = Lat<Q>::c(p, i);
+      if (ci == 0) continue;
+      x += ci > 0 ? U[i] : -U[i];
+#pragma unroll
+      for (int j = 0; j < D; j++) {
+        const int cj = Lat<Q>::c(p, j);
+        if (cj != 0) cbc += ci * cj > 0 ? Bh[i][j] : -Bh[i][j];
+        // 3 (c^j)^2 - 1 is 2 for an in-plane j and -1 otherwise
+        if (j != i) x += R((cj != 0 ? 2 : -1) * ci) * C2h[j][i];
+      }
+    }
+    xe[p] = cbc - tB3;
+    xo[p] = x;
   }
   // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a - L^j_a) f^eq_a   (Eq. 30):
   // K_a - L_a = K_a + K_abar = M_p, and a pair contributes c_p (f_p - f_pbar)
-  // with f_p - f_pbar = 2 rho w_p xo_p. The record holds am M_p with
-  // am = -(2 - 1/tau)/4, and -1/2 (1 - 1/(2 tau)) 2 rho = 2 rho am.
-  const R r2 = R(2) * rho;
+  // with f_p - f_pbar = 2 rho w_p xo_p = 6 rho w_p (xo_p / 3). The record holds
+  // am M_p with am = -(2 - 1/tau)/4, and -1/2 (1 - 1/(2 tau)) 2 rho = 2 rho am.
+  const R r6 = R(6) * rho;
   R dP[D][D];
 #pragma unroll
   for (int i = 0; i < D; i++)
@@ -227,7 +271,7 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
     for (int j = 0; j < D; j++) dP[i][j] = R(0);
 #pragma unroll
   for (int p = 1; p <= H; p++) {
-    const R df = r2 * lat_w<Q, R>(p) * xo[p];
+    const R df = r6 * lat_w<Q, R>(p) * xo[p];
 #pragma unroll
     for (int j = 0; j < D; j++) {
       const R amM = rc[L::mp(p, j)];
@@ -245,7 +289,7 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
   const R J = rc[L::J];
   {
     const R w = lat_w<Q, R>(0);
-    const R neq = (d[0] - w * mdev) - (w * m) * xe[0];
+    const R neq = (d[0] - w * mdev) - (R(3) * w * m) * xe[0];
     dp[0] = d[0] - itau * neq - (R(3) * w * J) * tr;
   }
 #pragma unroll
@@ -266,7 +310,7 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
     const R w = lat_w<Q, R>(p);
     const R Ep = (R(9) * w * J) * cPc - (R(3) * w * J) * tr;
     const R Op = (R(3) * w) * cF;
-    const R wd = w * mdev, wm = w * m;
+    const R wd = w * mdev, wm = (R(3) * w) * m;
     const R neqp = (d[p] - wd) - wm * (xe[p] + xo[p]);
     const R neqm = (d[p + H] - wd) - wm * (xe[p] - xo[p]);
     dp[p] = d[p] - itau * neqp + (Ep + Op);
