@@ -164,14 +164,20 @@ __device__ __forceinline__ __nv_bfloat16 s16_from_bits<__nv_bfloat16>(unsigned s
 
 // REFOFS: 16-bit populations stored relative to the local rest state (the
 // offsets from the uniform reference come with the record, plane mode only).
+// HPAR: 16-bit storage with an even cell count and an even fastest axis, so
+// that which half of its 32-bit word a value sits in follows from the cell's
+// own parity: a neighbour along a slow axis (or behind a wall: the own cell)
+// has the same parity, one along the fastest axis (periodic wrap included:
+// nfast - 1 is odd) the other one.
 // The tiles [t0, t1) of one mesh, as one block.
-template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, typename IT>
+template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, bool HPAR, typename IT>
 __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, const int64_t t1) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
   constexpr int RS = L::template stride<R>();
   constexpr bool H16 = sizeof(S) == 2;
   static_assert(!REFOFS || (PLANE && H16), "storage offsets need plane mode and 16-bit storage");
+  static_assert(!HPAR || H16, "half parity applies to 16-bit storage");
   // 16-byte pieces of the record that the kernel reads
   constexpr int RCHUNK = (REFOFS ? RS : L::ROWN) * (int)sizeof(R) / 16;
   static_assert(RCHUNK <= kStepThreads, "record larger than one copy per thread");
@@ -189,7 +195,12 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
     const IT ifast = (IT)c.tf * kStepThreads + (IT)tid;
     if (ifast < nfast) {
       const Addr<Q, IT> ad = tile_addr<Q, IT>(a.g, c, ifast);
-      if constexpr (H16) {
+      if constexpr (H16 && HPAR) {
+#pragma unroll
+        for (int av = 0; av < Q; av++)
+          cp_async<4>(&sm.pop[st][av][tid],
+                      reinterpret_cast<const uint32_t *>(f) + (src_index<Q, ODD, IT>(ps, ad, av) >> 1));
+      } else if constexpr (H16) {
         uint32_t hi = 0;
 #pragma unroll
         for (int av = 0; av < Q; av++) {
@@ -247,11 +258,19 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
 
       R N[Q];
       if constexpr (H16) {
-        const uint32_t hi = sm.half_hi[st][tid];
+        const uint32_t hi = HPAR ? 0u : sm.half_hi[st][tid];
+        // HPAR: the shift of the own cell's half and of the other one
+        const unsigned sh0 = ((unsigned)cell & 1u) << 4, sh1 = 16u - sh0;
 #pragma unroll
         for (int av = 0; av < Q; av++) {
           const uint32_t w = sm.pop[st][av][tid];
-          const unsigned short b = (unsigned short)(((hi >> av) & 1) ? (w >> 16) : (w & 0xffffu));
+          unsigned short b;
+          if constexpr (HPAR) {
+            const bool shifted = ODD && Lat<Q>::c(av, D - 1) != 0 && !ad.crosses(av, -1);
+            b = (unsigned short)(w >> (shifted ? sh1 : sh0));
+          } else {
+            b = (unsigned short)(((hi >> av) & 1) ? (w >> 16) : (w & 0xffffu));
+          }
           N[av] = load_s<R>(s16_from_bits<S>(b));
           if constexpr (REFOFS) {
             // back to the uniform reference: add the storage offset of the location
@@ -315,13 +334,13 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
 }
 
 // One mesh: block b walks the tiles [b per_block, (b + 1) per_block).
-template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, typename IT>
+template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, bool HPAR, typename IT>
 __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>())
     k_step(const __grid_constant__ StepArgs a) {
   const int64_t t0 = (int64_t)blockIdx.x * a.per_block;
   const int64_t t1 = t0 + a.per_block < a.ntiles ? t0 + a.per_block : a.ntiles;
   if (t0 >= t1) return;
-  step_tiles<Q, S, R, ODD, PLANE, REFOFS, IT>(a, t0, t1);
+  step_tiles<Q, S, R, ODD, PLANE, REFOFS, HPAR, IT>(a, t0, t1);
 }
 
 // Many meshes in one launch: block b takes the run of tiles items[b] of mesh
@@ -336,7 +355,7 @@ template <int Q, typename S, typename R, bool ODD, bool PLANE, typename IT>
 __global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>())
     k_step_batch(const StepArgs *__restrict__ args, const BatchItem *__restrict__ items) {
   const BatchItem it = items[blockIdx.x];
-  step_tiles<Q, S, R, ODD, PLANE, false, IT>(args[it.sim], it.t0, it.t1);
+  step_tiles<Q, S, R, ODD, PLANE, false, false, IT>(args[it.sim], it.t0, it.t1);
 }
 
 // Arguments of one simulation's step kernel (per_block left for the caller).
@@ -406,32 +425,44 @@ cudaError_t launch_step_t(const vlb_sim *sim, int odd, cudaStream_t s) {
     const int64_t nblk = (a.ntiles + a.per_block - 1) / a.per_block;
     kern<<<(unsigned)nblk, kStepThreads, smem, s>>>(a);
   };
-  auto pick = [&](auto plane_tag, auto ref_tag) {
+  auto pick = [&](auto plane_tag, auto ref_tag, auto par_tag) {
     constexpr bool P = decltype(plane_tag)::value, RO = decltype(ref_tag)::value;
+    constexpr bool HP = decltype(par_tag)::value;
     if (i32) {
       if (odd)
-        go(k_step<Q, S, R, true, P, RO, int32_t>);
+        go(k_step<Q, S, R, true, P, RO, HP, int32_t>);
       else
-        go(k_step<Q, S, R, false, P, RO, int32_t>);
+        go(k_step<Q, S, R, false, P, RO, HP, int32_t>);
     } else {
       if (odd)
-        go(k_step<Q, S, R, true, P, RO, int64_t>);
+        go(k_step<Q, S, R, true, P, RO, HP, int64_t>);
       else
-        go(k_step<Q, S, R, false, P, RO, int64_t>);
+        go(k_step<Q, S, R, false, P, RO, HP, int64_t>);
     }
   };
+  const std::true_type yes;
+  const std::false_type no;
   if constexpr (sizeof(S) == 2) {
+    // the half of a 16-bit value follows from the cell parity when both the
+    // cell count and the fastest axis are even
+    const bool par = m->ncell % 2 == 0 && m->md.n[m->md.dim - 1] % 2 == 0;
+    auto pick_par = [&](auto plane_tag, auto ref_tag) {
+      if (par)
+        pick(plane_tag, ref_tag, yes);
+      else
+        pick(plane_tag, ref_tag, no);
+    };
     if (a.plane && sim->ref_rest)
-      pick(std::true_type{}, std::true_type{});
+      pick_par(yes, yes);
     else if (a.plane)
-      pick(std::true_type{}, std::false_type{});
+      pick_par(yes, no);
     else
-      pick(std::false_type{}, std::false_type{});
+      pick_par(no, no);
   } else {
     if (a.plane)
-      pick(std::true_type{}, std::false_type{});
+      pick(yes, no, no);
     else
-      pick(std::false_type{}, std::false_type{});
+      pick(no, no, no);
   }
   return cudaGetLastError();
 }

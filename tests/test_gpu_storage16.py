@@ -32,9 +32,11 @@ def V():
     return vlb
 
 
-@pytest.fixture(scope="module")
-def channel():
-    mesh = W.channel_mesh(16, 12, 8, stretch=0.7, bump=0.05)
+# An even fastest axis lets the kernel tell a 16-bit value's half from the
+# cell parity; an odd one takes the path that records the half per value.
+@pytest.fixture(scope="module", params=[(16, 12, 8), (15, 12, 7)], ids=["even-rows", "odd-rows"])
+def channel(request):
+    mesh = W.channel_mesh(*request.param, stretch=0.7, bump=0.05)
     prm = W.params(0.6, body_force=(1e-5, 0, 0))
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
     o = OracleSim(mesh, prm)
