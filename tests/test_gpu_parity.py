@@ -388,3 +388,38 @@ def test_error_paths(V):
     s2 = V.Sim(good, W.params(0.8), rho, u)
     s2.step(2)
     s2.sync()
+
+
+def test_64bit_offsets_match_tiled_short_mesh(V):
+    """A mesh with Q x ncell >= 2^31 (117 M cells, D3Q19 FP32, plane mode)
+    runs the kernels with 64-bit offsets. Its initial fields repeat along the
+    periodic fastest axis with period 8 and its geometry does not vary along
+    it, so after every step its fields must equal, bit for bit, those of the
+    8 x 8 x 8 mesh with the same fields (32-bit offsets) tiled along that
+    axis: after an even and after an odd step of the A-A scheme."""
+    n2 = 14336 * 128
+    assert 19 * 8 * 8 * n2 >= 2 ** 31
+    small = W.channel_mesh(8, 8, 8, stretch=0.7, bump=0.05)
+    prm = W.params(0.8, body_force=(1e-5, 0, 0))
+    rho_s, u_s = W.noise_fields(small, amp=0.01, seed=9)
+    gs = V.Sim(V.Mesh(small), prm, rho_s, u_s, precision=V.VLB_F32)
+    big = W.channel_mesh(8, 8, n2, stretch=0.7, bump=0.05)
+    reps = n2 // 8
+    rho_b = np.tile(rho_s.reshape(8, 8, 1, 8), (1, 1, reps, 1)).reshape(-1)
+    u_b = np.tile(u_s.reshape(8, 8, 1, 8, 3), (1, 1, reps, 1, 1)).reshape(-1, 3)
+    mb_mesh = V.Mesh(big)
+    del big
+    gb = V.Sim(mb_mesh, prm, rho_b, u_b, precision=V.VLB_F32)
+    del rho_b, u_b
+    assert gb.layout()["plane"] and gs.layout()["plane"]
+    for parity in ("even", "odd"):
+        gs.step(1)
+        gb.step(1)
+        ms, mb = gs.moments(), gb.moments()
+        for key, shape in (("rho", (8, 8, 1, 8)), ("u", (8, 8, 1, 8, 3)), ("u_tilde", (8, 8, 1, 8, 3))):
+            small_f = ms[key].reshape(shape)
+            big_f = mb[key].reshape((8, 8, reps, 8) + shape[4:])
+            assert np.array_equal(big_f, np.broadcast_to(small_f, big_f.shape)), (parity, key)
+        del mb
+    gb.close()
+    mb_mesh.close()
