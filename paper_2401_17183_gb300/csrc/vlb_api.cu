@@ -371,19 +371,12 @@ int vlb_moments(vlb_sim *s, double *rho, double *u, double *u_tilde, double *tot
       totals[4 + d] = t7[4 + d];
     }
   }
-  if (rho || u || u_tilde) {
-    const size_t rec = 1 + 2 * dim;
-    // strided copies straight into the caller's arrays
-    if (rho)
-      CU(cudaMemcpy2D(rho, sizeof(double), s->d_fields, sizeof(double) * rec, sizeof(double), nc,
-                      cudaMemcpyDeviceToHost));
-    if (u)
-      CU(cudaMemcpy2D(u, sizeof(double) * dim, s->d_fields + 1, sizeof(double) * rec,
-                      sizeof(double) * dim, nc, cudaMemcpyDeviceToHost));
-    if (u_tilde)
-      CU(cudaMemcpy2D(u_tilde, sizeof(double) * dim, s->d_fields + 1 + dim, sizeof(double) * rec,
-                      sizeof(double) * dim, nc, cudaMemcpyDeviceToHost));
-  }
+  // the kernel writes rho [nc], u [nc][dim] and u~ [nc][dim] one after the
+  // other: one contiguous copy each, straight into the caller's arrays
+  if (rho) CU(cudaMemcpy(rho, s->d_fields, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+  if (u) CU(cudaMemcpy(u, s->d_fields + nc, sizeof(double) * nc * dim, cudaMemcpyDeviceToHost));
+  if (u_tilde)
+    CU(cudaMemcpy(u_tilde, s->d_fields + nc * (1 + dim), sizeof(double) * nc * dim, cudaMemcpyDeviceToHost));
   return VLB_OK;
 }
 

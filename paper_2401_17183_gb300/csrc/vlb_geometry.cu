@@ -343,7 +343,8 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
       N[av] = rec[L::J] * lat_w<Q, double>(av) * eq_even<Q, double>(e, p);
     }
     CollideState<Q, double> cs;
-    collide_cell<Q, double, false, false>(N, rec, 0.0, 1.0 / a.tau, 1e-15, 400, Np, cs);
+    // chord iteration from F = 0 (the record's FR is still zero here)
+    collide_cell<Q, double, true, false>(N, rec, 0.0, 1.0 / a.tau, 1e-15, 400, Np, cs);
     for (int i = 0; i < D; i++) rec[L::FR + i] = cs.conv ? cs.F[i] : 0.0;
   }
   // storage references: the rest state of Eq. 33 at the column that holds each

@@ -388,7 +388,7 @@ struct vlb_sim {
   vlb_params p;
   cudaStream_t stream = nullptr;
   void *d_f = nullptr;        // populations [q][ncell]
-  void *d_coef = nullptr;     // coefficient records [NC][ncoef]
+  void *d_coef = nullptr;     // coefficient records, record r at r * nc elements
   int64_t ncoef = 0;
   int32_t nc = 0;
   int32_t plane = 0;
@@ -396,7 +396,7 @@ struct vlb_sim {
   double nref = 0.0;          // populations are stored as N_a - w_a nref, nref = rho_0 J_ref
   int32_t ref_rest = 0;       // 16-bit storage relative to the local rest state
   int *d_err = nullptr;       // sticky kernel error flags
-  double *d_fields = nullptr; // moments output staging [ncell][1 + 2 dim]
+  double *d_fields = nullptr; // moments output staging: rho [ncell], u and u~ [ncell][dim]
   double *d_partial = nullptr;
   double *d_totals = nullptr;
   int64_t partial_blocks = 0;

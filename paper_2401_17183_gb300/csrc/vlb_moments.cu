@@ -11,8 +11,13 @@ struct MomArgs {
   const void *f;
   Grid g;
   int64_t ncell;
-  const double *J, *gl, *gu, *ginv, *K;
-  double body[3];
+  const double *gl;
+  // the simulation's coefficient records (FP64 or FP32; one per cell, or one
+  // per column of the fastest axis in plane mode)
+  const void *coef;
+  int32_t coef_f64, plane;
+  int64_t nfast;
+  int64_t rs;
   double rot[3][9];
   int32_t has_rot[3];
   int32_t periodic[3];
@@ -51,7 +56,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
 template <int Q, typename S, bool ODD>
 __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double *out,
                                                          double *partial) {
-  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2;
+  constexpr int D = Lat<Q>::D;
   const S *f = static_cast<const S *>(a.f);
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.ncell;
@@ -59,25 +64,28 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
     const Addr<Q> ad(a.g, c);
     double N[Q];
     pull_abs<Q, ODD, S>(f, a.ncell, ad, a.ref, N);
-    double K[Q][D], G[D], rec[CoefLayout<Q>::NC];
-    for (int av = 0; av < Q; av++)
-      for (int i = 0; i < D; i++) K[av][i] = a.K[(c * Q + av) * D + i];
-    for (int i = 0; i < D; i++) {
-      double s = 0.0;
-      for (int d = 0; d < D; d++) s += a.body[d] * a.gu[(c * D + i) * D + d];
-      G[i] = s;
+    // the cell's coefficient record, in FP64
+    double rec[CoefLayout<Q>::NC];
+    const int64_t r = a.plane ? c / a.nfast : c;
+    if (a.coef_f64) {
+      const double *src = static_cast<const double *>(a.coef) + r * a.rs;
+      for (int k = 0; k < CoefLayout<Q>::NC; k++) rec[k] = src[k];
+    } else {
+      const float *src = static_cast<const float *>(a.coef) + r * a.rs;
+      for (int k = 0; k < CoefLayout<Q>::NC; k++) rec[k] = static_cast<double>(src[k]);
     }
-    build_record<Q>(a.J[c], a.ginv + c * NS, G, K, a.tau, rec);
     double Np[Q];
     CollideState<Q, double> st;
-    // plain fixed point from F = 0 on the full populations (n_ref = 0)
-    collide_cell<Q, double, false, false>(N, rec, 0.0, 1.0 / a.tau, 1e-14, 200, Np, st);
+    // chord iteration from the record's rest-state start value on the full
+    // populations (n_ref = 0)
+    collide_cell<Q, double, true, false>(N, rec, 0.0, 1.0 / a.tau, 1e-14, 200, Np, st);
     if (!st.conv) atomicOr(a.err, ERR_NOCONV);
     double gl[D][D];
     for (int i = 0; i < D; i++)
       for (int d = 0; d < D; d++) gl[i][d] = a.gl[(c * D + i) * D + d];
-    double *o = out + c * (1 + 2 * D);
-    o[0] = st.rho;
+    // fields as three arrays: rho [ncell], u [ncell][D], u~ [ncell][D]
+    double *o_u = out + a.ncell + c * D, *o_ut = out + a.ncell * (1 + D) + c * D;
+    out[c] = st.rho;
     bool finite = isfinite(st.rho);
     for (int d = 0; d < D; d++) {
       double uu = 0.0, ut = 0.0;
@@ -85,8 +93,8 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
         uu += st.U[i] * gl[i][d];                                   // u = U^i g_i (Eq. 34)
         ut += (st.U[i] + 0.5 * (st.F[i] / st.rho)) * gl[i][d];      // u~ = U~^i g_i
       }
-      o[1 + d] = uu;
-      o[1 + D + d] = ut;
+      o_u[d] = uu;
+      o_ut[d] = ut;
       finite = finite && isfinite(uu) && isfinite(ut);
     }
     if (!finite) atomicOr(a.err, ERR_NONFINITE);
@@ -148,13 +156,13 @@ static cudaError_t moments_t(const vlb_sim *sim, double *d_out, double *d_partia
   a.f = sim->d_f;
   a.g = make_grid(m);
   a.ncell = m->ncell;
-  a.J = m->d_J;
   a.gl = m->d_gl;
-  a.gu = m->d_gu;
-  a.ginv = m->d_ginv;
-  a.K = m->d_K;
+  a.coef = sim->d_coef;
+  a.coef_f64 = arith_f64(sim->p.precision) ? 1 : 0;
+  a.plane = sim->plane;
+  a.nfast = m->md.n[m->md.dim - 1];
+  a.rs = sim->nc;
   for (int d = 0; d < 3; d++) {
-    a.body[d] = sim->p.body_force[d];
     a.has_rot[d] = m->md.has_rot[d];
     a.periodic[d] = (d < m->md.dim && m->md.bc[d] == VLB_PERIODIC) ? 1 : 0;
     for (int k = 0; k < 9; k++) a.rot[d][k] = m->md.rot[d][k];
