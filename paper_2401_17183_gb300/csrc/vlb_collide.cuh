@@ -145,7 +145,7 @@ __device__ void build_record(double J, const double *ginv, const double *G,
       for (int l = 0; l < D; l++) {
         const double pe = 1.5 * itau * Rt[i][k][l];
         ce += T0 * pe * gd[k][l];
-        if (k <= l) rec[L::PE + i * NS + sym<D>(k, l)] = (k == l ? 1.0 : 2.0) * pe;
+        if (k <= l) rec[L::row(L::PE, NS, i, sym<D>(k, l))] = (k == l ? 1.0 : 2.0) * pe;
       }
     rec[L::CE + i] = ce;
     for (int l = 0; l < D; l++) {
@@ -160,7 +160,7 @@ __device__ void build_record(double J, const double *ginv, const double *G,
         double s = 0.0;
         for (int p = 1; p <= H; p++) s += Ao[p][i] * c[p][l] * (3.0 * c[p][k] * c[p][k] - 1.0);
         PO2[i][k][l] = 4.5 * s;
-        rec[L::PO2 + i * L::NO + offd<D>(k, l)] = PO2[i][k][l];
+        rec[L::row(L::PO2, L::NO, i, offd<D>(k, l))] = PO2[i][k][l];
       }
   }
   for (int i = 0; i < D; i++)
@@ -175,15 +175,15 @@ __device__ void build_record(double J, const double *ginv, const double *G,
       }
       LO[i][j] = lo;
       TL[i][j] = tt + 0.5 * ld;
-      rec[L::LO + i * D + j] = lo;
-      rec[L::TL + i * D + j] = TL[i][j];
+      rec[L::row(L::LO, D, i, j)] = lo;
+      rec[L::row(L::TL, D, i, j)] = TL[i][j];
     }
   double A[D][D], Hm[D][D];
   for (int i = 0; i < D; i++)
     for (int j = 0; j < D; j++) A[i][j] = (i == j ? 1.0 : 0.0) + 0.25 * LO[i][j] + 0.5 * TL[i][j];
   inverse_small<D>(A, Hm);
   for (int i = 0; i < D; i++)
-    for (int j = 0; j < D; j++) rec[L::HM + i * D + j] = Hm[i][j];
+    for (int j = 0; j < D; j++) rec[L::row(L::HM, D, i, j)] = Hm[i][j];
 }
 
 // x y = p + e exactly (FMA two-product)
@@ -311,10 +311,21 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
     const R Ep = (R(9) * w * J) * cPc - (R(3) * w * J) * tr;
     const R Op = (R(3) * w) * cF;
     const R wd = w * mdev, wm = (R(3) * w) * m;
-    const R neqp = (d[p] - wd) - wm * (xe[p] + xo[p]);
-    const R neqm = (d[p + H] - wd) - wm * (xe[p] - xo[p]);
-    dp[p] = d[p] - itau * neqp + (Ep + Op);
-    dp[p + H] = d[p + H] - itau * neqm + (Ep - Op);
+    if constexpr (sizeof(R) == 4) {
+      // the pair in the two lanes of packed FP32 instructions (same roundings)
+      const float2 dd = make_float2(d[p], d[p + H]);
+      const float2 xs = __fadd2_rn(make_float2(xe[p], xe[p]), make_float2(xo[p], -xo[p]));
+      const float2 nq = __ffma2_rn(make_float2(-wm, -wm), xs, __fadd2_rn(dd, make_float2(-wd, -wd)));
+      const float2 r = __fadd2_rn(__ffma2_rn(make_float2(-itau, -itau), nq, dd),
+                                  __fadd2_rn(make_float2(Ep, Ep), make_float2(Op, -Op)));
+      dp[p] = r.x;
+      dp[p + H] = r.y;
+    } else {
+      const R neqp = (d[p] - wd) - wm * (xe[p] + xo[p]);
+      const R neqm = (d[p + H] - wd) - wm * (xe[p] - xo[p]);
+      dp[p] = d[p] - itau * neqp + (Ep + Op);
+      dp[p + H] = d[p + H] - itau * neqm + (Ep - Op);
+    }
   }
 }
 
@@ -405,23 +416,47 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
 #pragma unroll
       for (int l = k; l < D; l++) UU[sym<D>(k, l)] = Ut[k] * Ut[l];
     R r[D];
+    int i0 = 0;
+    if constexpr (sizeof(R) == 4) {
+      // rows 0 and 1 in the two lanes of packed FP32 instructions
+      auto ld2 = [&](int idx) { return *reinterpret_cast<const float2 *>(rc + idx); };
+      auto bc = [](float v) { return make_float2(v, v); };
+      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < D; i++) {
-      R a = R(0);
-#pragma unroll
-      for (int s = 0; s < NS; s++) a += rc[L::PE + i * NS + s] * UU[s];
+      for (int s = 0; s < NS; s++) a = __ffma2_rn(ld2(L::row(L::PE, NS, 0, s)), bc(UU[s]), a);
 #pragma unroll
       for (int k = 0; k < D; k++)
 #pragma unroll
         for (int l = 0; l < D; l++) {
           if (k == l) continue;
-          a += rc[L::PO2 + i * L::NO + offd<D>(k, l)] * (Ut2[k] * Ut[l]);
+          a = __ffma2_rn(ld2(L::row(L::PO2, L::NO, 0, offd<D>(k, l))), bc(Ut2[k] * Ut[l]), a);
         }
 #pragma unroll
-      for (int j = 0; j < D; j++) a += rc[L::LO + i * D + j] * Ut[j];
+      for (int j = 0; j < D; j++) a = __ffma2_rn(ld2(L::row(L::LO, D, 0, j)), bc(Ut[j]), a);
+#pragma unroll
+      for (int j = 0; j < D; j++) b = __ffma2_rn(ld2(L::row(L::TL, D, 0, j)), bc(Phi[j]), b);
+      r[0] = (Pb[0] - R(0.5) * (m * a.x + b.x)) - Phi[0];
+      r[1] = (Pb[1] - R(0.5) * (m * a.y + b.y)) - Phi[1];
+      i0 = 2;
+    }
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      if (i < i0) continue;
+      R a = R(0);
+#pragma unroll
+      for (int s = 0; s < NS; s++) a += rc[L::row(L::PE, NS, i, s)] * UU[s];
+#pragma unroll
+      for (int k = 0; k < D; k++)
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+          if (k == l) continue;
+          a += rc[L::row(L::PO2, L::NO, i, offd<D>(k, l))] * (Ut2[k] * Ut[l]);
+        }
+#pragma unroll
+      for (int j = 0; j < D; j++) a += rc[L::row(L::LO, D, i, j)] * Ut[j];
       R b = R(0);
 #pragma unroll
-      for (int j = 0; j < D; j++) b += rc[L::TL + i * D + j] * Phi[j];
+      for (int j = 0; j < D; j++) b += rc[L::row(L::TL, D, i, j)] * Phi[j];
       r[i] = (Pb[i] - R(0.5) * (m * a + b)) - Phi[i];
     }
     it++;
@@ -429,13 +464,25 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     // max(tol max(m, |Phi|), 64 eps |Phi|)
     R diff = R(0), pmax = R(0);
     R dF[D];
+    if constexpr (CHORD && sizeof(R) == 4) {
+      float2 x = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < D; j++)
+        x = __ffma2_rn(*reinterpret_cast<const float2 *>(rc + L::row(L::HM, D, 0, j)), make_float2(r[j], r[j]), x);
+      dF[0] = x.x;
+      dF[1] = x.y;
+    }
 #pragma unroll
     for (int i = 0; i < D; i++) {
       R x = r[i];
       if (CHORD) {
-        x = R(0);
+        if (sizeof(R) == 4 && i < 2) {
+          x = dF[i];
+        } else {
+          x = R(0);
 #pragma unroll
-        for (int j = 0; j < D; j++) x += rc[L::HM + i * D + j] * r[j];
+          for (int j = 0; j < D; j++) x += rc[L::row(L::HM, D, i, j)] * r[j];
+        }
       }
       dF[i] = x;
       diff = maxnan(diff, absr(x));

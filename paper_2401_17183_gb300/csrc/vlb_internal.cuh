@@ -97,6 +97,7 @@ __host__ __device__ constexpr int offd(int k, int l) {
 // as a polynomial in U~ (see build_record), so that one evaluation of the map
 // costs a few dozen products instead of a pass over all directions.
 __host__ __device__ constexpr int round4(int n) { return (n + 3) / 4 * 4; }
+__host__ __device__ constexpr int round2(int n) { return (n + 1) / 2 * 2; }
 
 template <int Q>
 struct CoefLayout {
@@ -116,18 +117,25 @@ struct CoefLayout {
   static constexpr int IJ = PO1 + D * D;       // 1 / J
   // link coefficients: am M_p^i at MPD + (p-1)*2D + i, ad D_p^i at MPD + (p-1)*2D + D + i
   static constexpr int MPD = round4(IJ + 1);
-  // one evaluation of the map
+  // one evaluation of the map: blocks of D rows (component i of Phi) of n
+  // coefficients each, stored with rows 0 and 1 interleaved (k-th pair at
+  // base + 2k, 8-byte aligned, for packed FP32 arithmetic) and row 2 after
+  // them; every block starts on an even element (see row())
   static constexpr int HM = round4(MPD + 2 * H * D);  // D x D chord matrix (I - L)^-1
-  static constexpr int PE = HM + D * D;        // D x NS: coefficient of U~^k U~^l (k <= l)
-  static constexpr int PO2 = PE + D * NS;      // D x NO: coefficient of (U~^k)^2 U~^l (k != l)
-  static constexpr int LO = PO2 + D * NO;      // D x D: coefficient of U~
-  static constexpr int TL = LO + D * D;        // D x D: coefficient of J F
+  static constexpr int PE = HM + round2(D * D);       // D x NS: coefficient of U~^k U~^l (k <= l)
+  static constexpr int PO2 = PE + round2(D * NS);     // D x NO: coefficient of (U~^k)^2 U~^l (k != l)
+  static constexpr int LO = PO2 + round2(D * NO);     // D x D: coefficient of U~
+  static constexpr int TL = LO + round2(D * D);       // D x D: coefficient of J F
+  // element k of row i of the block that starts at base and has n per row
+  __host__ __device__ static constexpr int row(int base, int n, int i, int k) {
+    return i < 2 ? base + 2 * k + i : base + 2 * n + (i - 2) * n + k;
+  }
   // storage references of 16-bit populations (reference VLB_REF_REST, plane
   // mode), as offsets from the uniform reference, r - w_a n_ref: at the cell's
   // own locations, at the location each population of an odd step is read
   // from (slot abar of q - c_a), and at the one it is written to (slot a of
   // q + c_a); a link through a wall reads and writes the cell's own slot
-  static constexpr int ROWN = round4(TL + D * D);
+  static constexpr int ROWN = round4(TL + round2(D * D));
   static constexpr int RIN = ROWN + Q;
   static constexpr int ROUT = RIN + Q;
   static constexpr int NC = ROUT + Q;
