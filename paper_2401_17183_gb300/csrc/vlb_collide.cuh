@@ -382,20 +382,40 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
   //   -1/2 (K_pbar d_p + K_p d_pbar) - 1/2 (1 - 1/tau)(K_p d_p + K_pbar d_pbar)
   //     = -(2 - 1/tau)/4 M_p s_p + (1/tau)/4 D_p t_p,
   // whose two weights the record's link coefficients already carry.
-  R Pb[D];
+  R Pb[D], s[D], pr[D];
 #pragma unroll
   for (int i = 0; i < D; i++) {
     const R kw = rc[L::KW + i];
-    const R pr = nref * kw;
-    const R err = two_prod_err(nref, kw, pr) + nref * rc[L::KWL + i];
-    R s = m * rc[L::BODY + i] - err - R(0.5) * itau * mdev * kw;
+    pr[i] = nref * kw;
+    const R err = two_prod_err(nref, kw, pr[i]) + nref * rc[L::KWL + i];
+    s[i] = m * rc[L::BODY + i] - err - R(0.5) * itau * mdev * kw;
+  }
+  int ipb = 0;
+  if constexpr (sizeof(R) == 4) {
+    // components 0 and 1 in the two lanes of packed FP32 instructions (the
+    // same roundings in the same order)
+    float2 s01 = make_float2(s[0], s[1]);
 #pragma unroll
-    for (int p = 1; p <= H; p++)
-      s = fmar(rc[L::dk(p, i)], tp[p], fmar(rc[L::mp(p, i)], sp[p], s));
+    for (int p = 1; p <= H; p++) {
+      s01 = __ffma2_rn(*reinterpret_cast<const float2 *>(rc + L::mp(p, 0)), make_float2(sp[p], sp[p]), s01);
+      s01 = __ffma2_rn(*reinterpret_cast<const float2 *>(rc + L::dk(p, 0)), make_float2(tp[p], tp[p]), s01);
+    }
+    s[0] = s01.x;
+    s[1] = s01.y;
+    ipb = 2;
+  }
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    if (i < ipb) continue;
+#pragma unroll
+    for (int p = 1; p <= H; p++) s[i] = fmar(rc[L::dk(p, i)], tp[p], fmar(rc[L::mp(p, i)], sp[p], s[i]));
+  }
+#pragma unroll
+  for (int i = 0; i < D; i++) {
     R u = rc[L::CE + i];
 #pragma unroll
     for (int l = 0; l < D; l++) u += rc[L::PO1 + i * D + l] * st.U[l];
-    Pb[i] = (s - R(0.5) * m * u) - pr;
+    Pb[i] = (s[i] - R(0.5) * m * u) - pr[i];
   }
   R Phi[D];
 #pragma unroll

@@ -115,7 +115,8 @@ struct CoefLayout {
   static constexpr int CE = UW + D;            // constant term of the map
   static constexpr int PO1 = CE + D;           // D x D: coefficient of U
   static constexpr int IJ = PO1 + D * D;       // 1 / J
-  // link coefficients: am M_p^i at MPD + (p-1)*2D + i, ad D_p^i at MPD + (p-1)*2D + D + i
+  // link coefficients, 2D per pair p: am M_p^0, am M_p^1, ad D_p^0, ad D_p^1,
+  // then (D = 3) am M_p^2, ad D_p^2 -- components 0 and 1 as 8-byte pairs
   static constexpr int MPD = round4(IJ + 1);
   // one evaluation of the map: blocks of D rows (component i of Phi) of n
   // coefficients each, stored with rows 0 and 1 interleaved (k-th pair at
@@ -139,8 +140,8 @@ struct CoefLayout {
   static constexpr int RIN = ROWN + Q;
   static constexpr int ROUT = RIN + Q;
   static constexpr int NC = ROUT + Q;
-  __host__ __device__ static constexpr int mp(int p, int i) { return MPD + (p - 1) * 2 * D + i; }
-  __host__ __device__ static constexpr int dk(int p, int i) { return MPD + (p - 1) * 2 * D + D + i; }
+  __host__ __device__ static constexpr int mp(int p, int i) { return MPD + (p - 1) * 2 * D + (i < 2 ? i : 4); }
+  __host__ __device__ static constexpr int dk(int p, int i) { return MPD + (p - 1) * 2 * D + (i < 2 ? 2 + i : 5); }
   // record stride in elements of type R: a multiple of four elements, so that
   // every record and group starts on a 16-byte boundary
   template <typename R>
