@@ -15,7 +15,8 @@ struct MomArgs {
   // the simulation's coefficient records (FP64 or FP32; one per cell, or one
   // per column of the fastest axis in plane mode)
   const void *coef;
-  int32_t coef_f64, plane;
+  int32_t plane;
+  double nref, tol;
   int64_t nfast;
   int64_t rs;
   double rot[3][9];
@@ -53,7 +54,10 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
   }
 }
 
-template <int Q, typename S, bool ODD>
+// MT: arithmetic of the per-cell solve for F -- FP64 for FP64 simulations,
+// FP32 (the step kernel's own arithmetic, on deviations from n_ref) for the
+// others; the output mapping and the conservation sums are FP64 throughout.
+template <int Q, typename S, bool ODD, typename MT>
 __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double *out,
                                                          double *partial) {
   constexpr int D = Lat<Q>::D;
@@ -64,34 +68,32 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
     const Addr<Q> ad(a.g, c);
     double N[Q];
     pull_abs<Q, ODD, S>(f, a.ncell, ad, a.ref, N);
-    // the cell's coefficient record, in FP64
-    double rec[CoefLayout<Q>::NC];
-    const int64_t r = a.plane ? c / a.nfast : c;
-    if (a.coef_f64) {
-      const double *src = static_cast<const double *>(a.coef) + r * a.rs;
-      for (int k = 0; k < CoefLayout<Q>::NC; k++) rec[k] = src[k];
-    } else {
-      const float *src = static_cast<const float *>(a.coef) + r * a.rs;
-      for (int k = 0; k < CoefLayout<Q>::NC; k++) rec[k] = static_cast<double>(src[k]);
-    }
-    double Np[Q];
-    CollideState<Q, double> st;
-    // chord iteration from the record's rest-state start value on the full
-    // populations (n_ref = 0)
-    collide_cell<Q, double, true, false>(N, rec, 0.0, 1.0 / a.tau, 1e-14, 200, Np, st);
+    // the cell's coefficient record (stored in MT) and its deviations from
+    // the uniform reference
+    const MT *rec = static_cast<const MT *>(a.coef) + (a.plane ? c / a.nfast : c) * a.rs;
+    MT dv[Q];
+#pragma unroll
+    for (int av = 0; av < Q; av++) dv[av] = static_cast<MT>(N[av] - lat_w<Q, double>(av) * a.nref);
+    MT Np[Q];
+    CollideState<Q, MT> st;
+    // chord iteration from the record's rest-state start value
+    collide_cell<Q, MT, true, false>(dv, rec, static_cast<MT>(a.nref), static_cast<MT>(1.0 / a.tau),
+                                     static_cast<MT>(a.tol), 200, Np, st);
     if (!st.conv) atomicOr(a.err, ERR_NOCONV);
     double gl[D][D];
     for (int i = 0; i < D; i++)
       for (int d = 0; d < D; d++) gl[i][d] = a.gl[(c * D + i) * D + d];
     // fields as three arrays: rho [ncell], u [ncell][D], u~ [ncell][D]
     double *o_u = out + a.ncell + c * D, *o_ut = out + a.ncell * (1 + D) + c * D;
-    out[c] = st.rho;
-    bool finite = isfinite(st.rho);
+    const double rho = st.rho;
+    out[c] = rho;
+    bool finite = isfinite(rho);
     for (int d = 0; d < D; d++) {
       double uu = 0.0, ut = 0.0;
       for (int i = 0; i < D; i++) {
-        uu += st.U[i] * gl[i][d];                                   // u = U^i g_i (Eq. 34)
-        ut += (st.U[i] + 0.5 * (st.F[i] / st.rho)) * gl[i][d];      // u~ = U~^i g_i
+        const double Ui = st.U[i], Fi = st.F[i];
+        uu += Ui * gl[i][d];                                        // u = U^i g_i (Eq. 34)
+        ut += (Ui + 0.5 * (Fi / rho)) * gl[i][d];                   // u~ = U~^i g_i
       }
       o_u[d] = uu;
       o_ut[d] = ut;
@@ -158,7 +160,8 @@ static cudaError_t moments_t(const vlb_sim *sim, double *d_out, double *d_partia
   a.ncell = m->ncell;
   a.gl = m->d_gl;
   a.coef = sim->d_coef;
-  a.coef_f64 = arith_f64(sim->p.precision) ? 1 : 0;
+  a.nref = sim->nref;
+  a.tol = sim->p.tol;
   a.plane = sim->plane;
   a.nfast = m->md.n[m->md.dim - 1];
   a.rs = sim->nc;
@@ -170,10 +173,11 @@ static cudaError_t moments_t(const vlb_sim *sim, double *d_out, double *d_partia
   a.tau = sim->p.tau;
   a.ref = make_ref(sim);
   a.err = sim->d_err;
+  using MT = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
   if (sim->t & 1)
-    k_moments<Q, S, true><<<(unsigned)nblk, kMomThreads, 0, s>>>(a, d_out, d_partial);
+    k_moments<Q, S, true, MT><<<(unsigned)nblk, kMomThreads, 0, s>>>(a, d_out, d_partial);
   else
-    k_moments<Q, S, false><<<(unsigned)nblk, kMomThreads, 0, s>>>(a, d_out, d_partial);
+    k_moments<Q, S, false, MT><<<(unsigned)nblk, kMomThreads, 0, s>>>(a, d_out, d_partial);
   return cudaGetLastError();
 }
 
