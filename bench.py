@@ -461,6 +461,9 @@ def main():
         out_u = torch.empty(ncell * 3, dtype=torch.float64).pin_memory()
         out_ut = torch.empty(ncell * 3, dtype=torch.float64).pin_memory()
         out_t = torch.empty(7, dtype=torch.float64).pin_memory()
+        # one untimed pass through the same buffers (first-touch of the pinned pages)
+        sim.reset_ptr(pin_rho.data_ptr(), pin_u.data_ptr())
+        sim.moments_ptr(out_rho.data_ptr(), out_u.data_ptr(), out_ut.data_ptr(), out_t.data_ptr())
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
