@@ -152,10 +152,17 @@ struct CoefLayout {
 
 constexpr double kT0 = 1.0 / 3.0;
 
-// max that propagates NaN from either side (a NaN residual never converges)
+// max that propagates NaN from either side (a NaN residual never converges);
+// FP32 in one instruction (PTX max.NaN)
 template <typename R>
 __device__ __forceinline__ R maxnan(R a, R b) {
   return (a > b || a != a) ? a : b;
+}
+template <>
+__device__ __forceinline__ float maxnan<float>(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
 }
 __device__ __forceinline__ float absr(float x) { return fabsf(x); }
 __device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
