@@ -285,29 +285,6 @@ __device__ __forceinline__ R eq_even(const EqParts<Q, R> &e, int a) {
   return R(1) + (R(3) * cbc - e.trB) * R(1.5);
 }
 
-// the same even part minus its leading 1: kept separate so that the large
-// constant never goes through a rounding together with the small terms
-template <int Q, typename R>
-__device__ __forceinline__ R eq_even_dev(const EqParts<Q, R> &e, int a) {
-  constexpr int D = Lat<Q>::D;
-  R cbc = R(0);
-#pragma unroll
-  for (int i = 0; i < D; i++) {
-    const int ci = Lat<Q>::c(a, i);
-    if (ci == 0) continue;
-#pragma unroll
-    for (int j = 0; j < D; j++) {
-      const int cj = Lat<Q>::c(a, j);
-      if (cj == 0) continue;
-      if (ci * cj > 0)
-        cbc += e.B[i][j];
-      else
-        cbc -= e.B[i][j];
-    }
-  }
-  return (R(3) * cbc - e.trB) * R(1.5);  // (c.B.c / T0 - tr B) / (2 T0)
-}
-
 // odd part of the bracket of Eq. 33 for direction a:
 //   c.U / T0 + (9/2) sum_{k != l} C^kkl c^l (3 (c^k)^2 - 1)
 template <int Q, typename R>

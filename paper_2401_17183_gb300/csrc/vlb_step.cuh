@@ -60,6 +60,7 @@ struct StepArgs {
   int64_t ntiles;
   int32_t ntf, nA, nB;
   int64_t per_block;  // tiles per block (contiguous runs)
+  int32_t full_tiles; // the fastest axis is a whole number of tiles
 };
 
 constexpr int kStepThreads = 128;
@@ -189,11 +190,30 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
   const IT nfast = (IT)(D == 3 ? a.g.n[2] : a.g.n[1]);
   const int tid = threadIdx.x;
 
+  // pieces of 16 bytes in one direction's row segment of a tile
+  constexpr int PER_ROW = kStepThreads * (int)sizeof(S) / 16;
+
   // issue this thread's copies for tile c into stage st: the populations of
-  // its cell and, in plane mode, one 16-byte piece of the shared record
+  // its cell and, in plane mode, one 16-byte piece of the shared record. On
+  // even steps of full tiles every direction reads the tile's own row
+  // segment, so the block copies the Q segments in 16-byte pieces instead
+  // (thread tid takes pieces tid, tid + 128, ...).
   auto prefetch = [&](const TileCursor &c, int st) {
     const IT ifast = (IT)c.tf * kStepThreads + (IT)tid;
-    if (ifast < nfast) {
+    bool rows = false;
+    if constexpr (!ODD && !H16) {
+      if (a.full_tiles) {
+        rows = true;
+        const IT cell0 = tile_addr<Q, IT>(a.g, c, (IT)c.tf * kStepThreads).cell;
+#pragma unroll
+        for (int k = tid; k < Q * PER_ROW; k += kStepThreads) {
+          const int av = k / PER_ROW, j = k - av * PER_ROW;
+          cp_async<16>(reinterpret_cast<unsigned char *>(&sm.pop[st][av][0]) + 16 * j,
+                       reinterpret_cast<const unsigned char *>(f + ((IT)av * ps + cell0)) + 16 * j);
+        }
+      }
+    }
+    if (!rows && ifast < nfast) {
       const Addr<Q, IT> ad = tile_addr<Q, IT>(a.g, c, ifast);
       if constexpr (H16 && HPAR) {
 #pragma unroll
@@ -389,6 +409,7 @@ inline StepArgs make_step_args(const vlb_sim *sim) {
   a.nB = (int32_t)(dim == 3 ? m->md.n[1] : m->md.n[0]);
   a.ntiles = (int64_t)a.ntf * a.nA * a.nB;
   a.per_block = 0;
+  a.full_tiles = nfast % kStepThreads == 0 ? 1 : 0;
   return a;
 }
 
