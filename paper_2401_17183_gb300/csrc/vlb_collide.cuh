@@ -33,6 +33,12 @@
 //   Pb' = Pb - 1/2 m (CE + PO1 U).
 // The post-collision populations themselves are formed once, at the converged
 // Phi, direction by direction.
+//
+// In FP32, pairs of identical operations run in the two lanes of packed FP32
+// instructions (sm_100 and later): a direction pair (p, pbar) of the final
+// pass, rows 0 and 1 of the map and of the chord correction, and components 0
+// and 1 of the constant part, each pair with the same roundings in the same
+// order as two scalar operations.
 #pragma once
 
 #include "vlb_internal.cuh"

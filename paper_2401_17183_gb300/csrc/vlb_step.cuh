@@ -17,7 +17,9 @@
 // The kernel is persistent: each block walks a contiguous run of tiles (128
 // consecutive cells along the fastest axis), and each thread copies the Q
 // populations of its cell in tile k + 2 into shared memory with asynchronous
-// copies while it collides its cell in tile k (three stages). The DRAM latency
+// copies while it collides its cell in tile k (three stages); on even steps of
+// full tiles, where every direction reads the tile's own row segment, the
+// block copies the Q segments in 16-byte pieces instead. The DRAM latency
 // of the reads is thereby hidden behind the arithmetic of a tile without
 // holding the loads in registers. In plane mode the tile's shared coefficient
 // record travels in the same copy group, in 16-byte pieces; one block barrier
