@@ -31,19 +31,77 @@ static const double W19[19] = {1.0 / 3.0,  1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1
                                1.0 / 18.0, 1.0 / 18.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
                                1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
                                1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-static const double T0 = 1.0 / 3.0;
+/* D3Q39: a velocity set with moment isotropy to 6th order (Eq. 10 in full),
+ * T0 = 2/3: the rest vector, the 6 unit axis vectors, the 8 corner vectors
+ * (+-1, +-1, +-1), 6 axis vectors of length 2, the 12 vectors (+-2, +-2, 0) and
+ * permutations, and 6 axis vectors of length 3; weights 1/12, 1/12, 1/27,
+ * 2/135, 1/432 and 1/1620 (a set from the literature on higher-order lattice
+ * Boltzmann models; the tests check Eq. 10 on it to 6th order exactly). */
+static int32_t C39[39][3];
+static double W39[39];
+static int c39_ready = 0;
+static void c39_fill(void) {
+  int k = 0;
+  C39[k][0] = C39[k][1] = C39[k][2] = 0;
+  W39[k++] = 1.0 / 12.0;
+  for (int d = 0; d < 3; d++)
+    for (int s = 1; s >= -1; s -= 2) {
+      C39[k][0] = C39[k][1] = C39[k][2] = 0;
+      C39[k][d] = s;
+      W39[k++] = 1.0 / 12.0;
+    }
+  for (int x = 1; x >= -1; x -= 2)
+    for (int y = 1; y >= -1; y -= 2)
+      for (int z = 1; z >= -1; z -= 2) {
+        C39[k][0] = x;
+        C39[k][1] = y;
+        C39[k][2] = z;
+        W39[k++] = 1.0 / 27.0;
+      }
+  for (int d = 0; d < 3; d++)
+    for (int s = 2; s >= -2; s -= 4) {
+      C39[k][0] = C39[k][1] = C39[k][2] = 0;
+      C39[k][d] = s;
+      W39[k++] = 2.0 / 135.0;
+    }
+  for (int d = 0; d < 3; d++)
+    for (int e = d + 1; e < 3; e++)
+      for (int s = 2; s >= -2; s -= 4)
+        for (int t = 2; t >= -2; t -= 4) {
+          C39[k][0] = C39[k][1] = C39[k][2] = 0;
+          C39[k][d] = s;
+          C39[k][e] = t;
+          W39[k++] = 1.0 / 432.0;
+        }
+  for (int d = 0; d < 3; d++)
+    for (int s = 3; s >= -3; s -= 6) {
+      C39[k][0] = C39[k][1] = C39[k][2] = 0;
+      C39[k][d] = s;
+      W39[k++] = 1.0 / 1620.0;
+    }
+  c39_ready = 1;
+}
 
-static const int32_t (*lat_c(int32_t q))[3] { return q == 9 ? C9 : C19; }
-static const double *lat_w(int32_t q) { return q == 9 ? W9 : W19; }
+static const int32_t (*lat_c(int32_t q))[3] {
+  if (q == 39 && !c39_ready) c39_fill();
+  return q == 9 ? C9 : q == 19 ? C19 : (const int32_t(*)[3])C39;
+}
+static const double *lat_w(int32_t q) {
+  if (q == 39 && !c39_ready) c39_fill();
+  return q == 9 ? W9 : q == 19 ? W19 : W39;
+}
 static int lat_dim(int32_t q) { return q == 9 ? 2 : 3; }
+/* the lattice constant T0 of Eq. 10 */
+static double lat_T0(int32_t q) { return q == 39 ? 2.0 / 3.0 : 1.0 / 3.0; }
+static int lat_known(int32_t q) { return q == 9 || q == 19 || q == 39; }
 
 /* index of the opposite direction c_abar = -c_a, found by search once */
-static int OPP9[9], OPP19[19], opp_ready = 0;
+static int OPP9[9], OPP19[19], OPP39[39], opp_ready = 0;
 static void opp_fill(void) {
-  for (int t = 0; t < 2; t++) {
-    int32_t q = t ? 19 : 9;
+  for (int t = 0; t < 3; t++) {
+    int32_t q = t == 0 ? 9 : t == 1 ? 19 : 39;
     const int32_t(*c)[3] = lat_c(q);
-    int *o = t ? OPP19 : OPP9;
+    int *o = t == 0 ? OPP9 : t == 1 ? OPP19 : OPP39;
     for (int a = 0; a < q; a++)
       for (int b = 0; b < q; b++)
         if (c[b][0] == -c[a][0] && c[b][1] == -c[a][1] && c[b][2] == -c[a][2]) o[a] = b;
@@ -52,13 +110,13 @@ static void opp_fill(void) {
 }
 static int opposite(int32_t q, int a) {
   if (!opp_ready) opp_fill();
-  return q == 9 ? OPP9[a] : OPP19[a];
+  return q == 9 ? OPP9[a] : q == 19 ? OPP19[a] : OPP39[a];
 }
 
 static double kd(int i, int j) { return i == j ? 1.0 : 0.0; }
 
 int vlbo_lattice(int32_t q, int32_t *c, double *w, double *t0) {
-  if (q != 9 && q != 19) return VLBO_EINVAL;
+  if (!lat_known(q)) return VLBO_EINVAL;
   const int32_t(*cc)[3] = lat_c(q);
   const double *ww = lat_w(q);
   for (int a = 0; a < q; a++) {
@@ -66,7 +124,7 @@ int vlbo_lattice(int32_t q, int32_t *c, double *w, double *t0) {
       for (int d = 0; d < 3; d++) c[3 * a + d] = cc[a][d];
     if (w) w[a] = ww[a];
   }
-  if (t0) *t0 = T0;
+  if (t0) *t0 = lat_T0(q);
   return VLBO_OK;
 }
 
@@ -205,7 +263,10 @@ static int dual_basis(int dim, const double gl[3][3], double *J, double gu[3][3]
 int vlbo_cell_geometry(const vlbo_mesh *m, const vlbo_params *prm, const int64_t qi[3],
                        vlbo_cell *out) {
   int dim = m->dim, q = m->q;
-  if ((dim == 2 && q != 9) || (dim == 3 && q != 19)) return VLBO_EINVAL;
+  if ((dim == 2 && q != 9) || (dim == 3 && q != 19 && q != 39)) return VLBO_EINVAL;
+  if (q == 39)
+    for (int d = 0; d < dim; d++)
+      if (m->bc[d] == VLBO_WALL) return VLBO_EINVAL; /* periodic meshes only */
   const int32_t(*c)[3] = lat_c(q);
   memset(out, 0, sizeof(*out));
   int rc = tangents(m, qi, out->g_low);
@@ -276,7 +337,8 @@ int vlbo_cell_geometry(const vlbo_mesh *m, const vlbo_params *prm, const int64_t
  * and each direction contracts them with its Hermite tensors. */
 int vlbo_equilibrium(int32_t q, double rho, const double U[3], const double Ut[3],
                      const double ginv[9], double *feq) {
-  if (q != 9 && q != 19) return VLBO_EINVAL;
+  if (!lat_known(q)) return VLBO_EINVAL;
+  const double T0 = lat_T0(q);
   int D = lat_dim(q);
   const int32_t(*c)[3] = lat_c(q);
   const double *w = lat_w(q);
@@ -319,6 +381,7 @@ static void collide_eval(int32_t q, const vlbo_cell *cell, double tau, const dou
   int D = lat_dim(q);
   const int32_t(*c)[3] = lat_c(q);
   const double *w = lat_w(q);
+  const double T0 = lat_T0(q);
   double J = cell->J;
   double Ut[3] = {0, 0, 0};
   /* U~ = U + a/2 with rho a = F (text after Eq. 32) */
@@ -374,7 +437,7 @@ static void collide_eval(int32_t q, const vlbo_cell *cell, double tau, const dou
 int vlbo_collide(int32_t q, const vlbo_cell *cell, const vlbo_params *p, const double *N,
                  double *Np_out, double *F_out, double *feq_out, double *dPi_out,
                  double *dN_out, double *Om_out, int32_t *iters_out) {
-  if (q != 9 && q != 19) return VLBO_EINVAL;
+  if (!lat_known(q)) return VLBO_EINVAL;
   int D = lat_dim(q);
   const int32_t(*c)[3] = lat_c(q);
   double J = cell->J;
@@ -451,11 +514,14 @@ static void cell_coords(const vlbo_mesh *m, int64_t idx, int64_t q[3]) {
 int vlbo_create(const vlbo_mesh *m, const vlbo_params *p, vlbo_sim **out) {
   *out = NULL;
   if (!m || !p || !m->x) return VLBO_EINVAL;
-  if (!((m->dim == 2 && m->q == 9) || (m->dim == 3 && m->q == 19))) return VLBO_EINVAL;
+  if (!((m->dim == 2 && m->q == 9) || (m->dim == 3 && (m->q == 19 || m->q == 39)))) return VLBO_EINVAL;
   if (m->dim == 2 && m->n[2] != 1) return VLBO_EINVAL;
   for (int a = 0; a < m->dim; a++) {
     if (m->n[a] < 1) return VLBO_EINVAL;
     if (m->bc[a] == VLBO_WALL && m->n[a] < 2) return VLBO_EINVAL;
+    /* D3Q39 (speeds up to 3): periodic axes of at least 3 cells only; halfway
+     * bounce-back is defined here for links that leave by one cell */
+    if (m->q == 39 && (m->bc[a] == VLBO_WALL || m->n[a] < 3)) return VLBO_EINVAL;
   }
   if (!(p->tau > 0.5)) return VLBO_EINVAL;
   vlbo_sim *s = (vlbo_sim *)calloc(1, sizeof(vlbo_sim));

@@ -33,6 +33,10 @@
  *   - an external body force G adds rho G.g^i to F^i inside the fixed point;
  *   - velocity sets: D3Q19 as listed in section 2.1 and its 2D restriction
  *     D2Q9, with the standard weights (the paper states none); T0 = 1/3.
+ *     D3Q39 (speeds up to 3; T0 = 2/3), a set that meets the isotropy
+ *     conditions of Eq. 10 to 6th order as the paper asks, so that the third
+ *     moment Q^eq of the equilibrium is matched exactly; periodic meshes
+ *     (every axis at least 3 cells) only.
  *
  * Parity pins: the test suite checks this library against closed forms,
  * moment identities, conservation laws, a textbook Cartesian LBM on the
@@ -58,14 +62,14 @@ extern "C" {
 #define VLBO_PERIODIC 0
 #define VLBO_WALL 1
 
-#define VLBO_QMAX 19
+#define VLBO_QMAX 39
 
 /* A structured mesh: node positions x(q) on the index lattice q (section 2.1).
  * x is C-ordered [n0][n1][n2][dim] (n2 = 1 when dim = 2) and is only borrowed
  * by vlbo_cell_geometry; vlbo_create copies it. */
 typedef struct {
   int32_t dim;             /* 2 or 3 */
-  int32_t q;               /* 9 (D2Q9, dim 2) or 19 (D3Q19, dim 3) */
+  int32_t q;               /* 9 (D2Q9, dim 2), 19 (D3Q19, dim 3) or 39 (D3Q39, dim 3) */
   int64_t n[3];
   const double *x;
   int32_t bc[3];           /* VLBO_PERIODIC or VLBO_WALL per axis */

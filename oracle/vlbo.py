@@ -11,7 +11,7 @@ import numpy as np
 
 from .build import build_oracle
 
-VLBO_QMAX = 19
+VLBO_QMAX = 39
 _lib = None
 
 

@@ -83,6 +83,20 @@ def periodic_sine_mesh(L=64, amp_frac=0.1):
     return _mesh(2, (L, L, 1), X, (PERIODIC, PERIODIC), shift=[[L, 0], [0, L]])
 
 
+def periodic_sine_mesh3d(L=16, amp_frac=0.01, q=19):
+    """3D periodic mapped box: x = xi + A sin(2 pi eta / L), y = eta + A sin(2 pi
+    zeta / L), z = zeta + A sin(2 pi xi / L); q selects the velocity set (19 or
+    39, the 6th-order isotropic set)."""
+    A = amp_frac * L
+    g = np.arange(L, dtype=np.float64)
+    xi, eta, zeta = np.meshgrid(g, g, g, indexing="ij")
+    X = np.stack([xi + A * np.sin(2 * np.pi * eta / L), eta + A * np.sin(2 * np.pi * zeta / L),
+                  zeta + A * np.sin(2 * np.pi * xi / L)], axis=-1)
+    m = _mesh(3, (L, L, L), X, (PERIODIC, PERIODIC, PERIODIC), shift=[[L, 0, 0], [0, L, 0], [0, 0, L]])
+    m["q"] = int(q)
+    return m
+
+
 def affine_mesh(A, n, b=None, dim=None):
     """Periodic affine mesh x = A q + b (every Theta vanishes)."""
     A = np.asarray(A, dtype=np.float64)
