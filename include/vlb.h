@@ -49,7 +49,13 @@ enum vlb_status {
   VLB_ENONFINITE = 6   /* non-finite population or moment detected */
 };
 
-enum vlb_lattice_kind { VLB_D2Q9 = 9, VLB_D3Q19 = 19 };
+/* D3Q39: moment isotropy to 6th order (Eq. 10 in full, T0 = 2/3), so that the
+ * equilibrium of Eq. 33 matches the third moment Q^eq of Eq. 32 exactly;
+ * speeds up to 3. Periodic meshes only (every axis at least 3 cells, no
+ * periodic rotation), FP64 populations, per-cell geometry; no batches and no
+ * vlb_totals_noalloc. The paper names no velocity set with this property;
+ * the weights are those of the published D3Q39 set. */
+enum vlb_lattice_kind { VLB_D2Q9 = 9, VLB_D3Q19 = 19, VLB_D3Q39 = 39 };
 enum vlb_bc { VLB_PERIODIC = 0, VLB_WALL = 1 };
 enum vlb_precision { VLB_F64 = 0, VLB_F32 = 1, VLB_F16 = 2, VLB_BF16 = 3 };
 enum vlb_reference { VLB_REF_UNIFORM = 0, VLB_REF_REST = 1 };
@@ -73,7 +79,7 @@ typedef struct vlb_sim vlb_sim;   /* opaque, library-owned */
  * the two nearest interior nodes along that axis. */
 typedef struct {
   int32_t dim;      /* 2 or 3 */
-  int32_t lattice;  /* VLB_D2Q9 with dim 2, VLB_D3Q19 with dim 3 */
+  int32_t lattice;  /* VLB_D2Q9 with dim 2, VLB_D3Q19 or VLB_D3Q39 with dim 3 */
   int64_t n[3];     /* nodes per index axis, each >= 1 (>= 2 on a wall axis); n[2] = 1 in 2D */
   const double *x;
   int32_t bc[3];

@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
 SOURCES = ["vlb_api.cu", "vlb_geometry.cu", "vlb_step.cu", "vlb_step16.cu", "vlb_batch.cu",
-           "vlb_moments.cu", "vlb_noalloc.cu", "vlb_nn.cu"]
-HEADERS = ["vlb_internal.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_step.cuh"]
+           "vlb_moments.cu", "vlb_noalloc.cu", "vlb_nn.cu", "vlb_q39.cu"]
+HEADERS = ["vlb_internal.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_step.cuh", "vlb_q39.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2"]

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "vlb_internal.cuh"
+#include "vlb_q39.cuh"
 
 namespace {
 
@@ -70,13 +71,17 @@ extern "C" {
 const char *vlb_last_error(void) { return g_err; }
 
 int vlb_lattice(int32_t lattice, int32_t *c, double *w) {
-  if (lattice != VLB_D2Q9 && lattice != VLB_D3Q19) return fail(VLB_EINVAL, "unknown lattice %d", lattice);
+  if (lattice != VLB_D2Q9 && lattice != VLB_D3Q19 && lattice != VLB_D3Q39)
+    return fail(VLB_EINVAL, "unknown lattice %d", lattice);
   for (int a = 0; a < lattice; a++) {
     for (int d = 0; d < 3; d++) {
-      const int v = lattice == 9 ? vlb::Lat<9>::c(a, d) : vlb::Lat<19>::c(a, d);
+      const int v = lattice == 9    ? vlb::Lat<9>::c(a, d)
+                    : lattice == 19 ? vlb::Lat<19>::c(a, d)
+                                    : vlb::Lat<39>::c(a, d);
       if (c) c[3 * a + d] = v;
     }
-    if (w) w[a] = lattice == 9 ? vlb::lat_w<9, double>(a) : vlb::lat_w<19, double>(a);
+    if (w)
+      w[a] = lattice == 9 ? vlb::lat_w<9, double>(a) : lattice == 19 ? vlb::lat_w<19, double>(a) : vlb::q39_w(a);
   }
   return VLB_OK;
 }
@@ -86,8 +91,15 @@ int vlb_mesh_create(const vlb_mesh_desc *desc, vlb_mesh **out) {
   *out = nullptr;
   if (!desc || !desc->x) return fail(VLB_EINVAL, "desc or desc->x is NULL");
   const int dim = desc->dim, q = desc->lattice;
-  if (!((dim == 2 && q == VLB_D2Q9) || (dim == 3 && q == VLB_D3Q19)))
-    return fail(VLB_EINVAL, "dim %d with lattice %d is not supported (D2Q9 in 2D, D3Q19 in 3D)", dim, q);
+  if (!((dim == 2 && q == VLB_D2Q9) || (dim == 3 && (q == VLB_D3Q19 || q == VLB_D3Q39))))
+    return fail(VLB_EINVAL, "dim %d with lattice %d is not supported (D2Q9 in 2D, D3Q19 or D3Q39 in 3D)", dim, q);
+  if (q == VLB_D3Q39)
+    for (int a = 0; a < 3; a++) {
+      if (desc->bc[a] != VLB_PERIODIC || desc->n[a] < 3)
+        return fail(VLB_EINVAL, "D3Q39 needs periodic axes of at least 3 cells (axis %d)", a);
+      for (int k = 0; k < 9; k++)
+        if (desc->period_rot[a][k] != 0.0) return fail(VLB_EINVAL, "D3Q39 takes no periodic rotations");
+    }
   if (dim == 2 && desc->n[2] != 1) return fail(VLB_EINVAL, "n[2] must be 1 in 2D");
   for (int a = 0; a < dim; a++) {
     if (desc->n[a] < 1) return fail(VLB_EINVAL, "n[%d] = %lld < 1", a, (long long)desc->n[a]);
@@ -156,9 +168,10 @@ int vlb_mesh_create(const vlb_mesh_desc *desc, vlb_mesh **out) {
   const int64_t nblk = std::min<int64_t>(1024, (nc + vlb::kStatThreads - 1) / vlb::kStatThreads);
   if (cudaMalloc(&d_part, sizeof(double) * 5 * nblk) != cudaSuccess)
     return cleanup(fail(VLB_ENOMEM, "stats scratch"));
-  e = vlb::launch_mesh_stats(m, d_part, nblk, 0);
+  e = q == VLB_D3Q39 ? vlb::q39_mesh_stats(m, d_part, nblk, 0) : vlb::launch_mesh_stats(m, d_part, nblk, 0);
   if (e != cudaSuccess) return cleanup(fail(VLB_ECUDA, "stats launch: %s", cudaGetErrorString(e)));
-  e = vlb::launch_plane_check(m, d_flag + 1, 0);
+  // D3Q39 keeps per-cell geometry (no plane records): report "varies"
+  e = q == VLB_D3Q39 ? cudaMemset(d_flag + 1, 1, sizeof(int)) : vlb::launch_plane_check(m, d_flag + 1, 0);
   if (e != cudaSuccess) return cleanup(fail(VLB_ECUDA, "plane check: %s", cudaGetErrorString(e)));
   double *h = new (std::nothrow) double[5 * nblk];
   if (!h) return cleanup(fail(VLB_ENOMEM, "host stats"));
@@ -236,7 +249,8 @@ static int upload_fields(vlb_sim *s, const double *rho, const double *u) {
   double *d_rho = s->d_io, *d_u = s->d_io + nc;
   CU(cudaMemcpyAsync(d_rho, rho, sizeof(double) * nc, cudaMemcpyHostToDevice, s->stream));
   CU(cudaMemcpyAsync(d_u, u, sizeof(double) * nc * dim, cudaMemcpyHostToDevice, s->stream));
-  CU(vlb::launch_init(s, d_rho, d_u, s->stream));
+  CU(s->mesh->md.q == VLB_D3Q39 ? vlb::q39_init(s, d_rho, d_u, s->stream)
+                                 : vlb::launch_init(s, d_rho, d_u, s->stream));
   CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
   s->t = 0;
   return VLB_OK;
@@ -255,6 +269,10 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
   if (params->coef_mode < VLB_COEF_AUTO || params->coef_mode > VLB_COEF_PLANE)
     return fail(VLB_EINVAL, "unknown coef_mode %d", params->coef_mode);
   const int dim = mesh->md.dim, q = mesh->md.q;
+  if (q == VLB_D3Q39 && params->precision != VLB_F64)
+    return fail(VLB_EINVAL, "D3Q39 runs in FP64 (precision VLB_F64)");
+  if (q == VLB_D3Q39 && params->coef_mode == VLB_COEF_PLANE)
+    return fail(VLB_EINVAL, "D3Q39 reads per-cell geometry (coef_mode AUTO or FULL)");
   bool moving = false;
   int nwall = 0;
   for (int a = 0; a < dim; a++) nwall += mesh->md.bc[a] == VLB_WALL;
@@ -295,19 +313,21 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
     s->ref_rest = 1;
   }
   const bool f64 = vlb::arith_f64(params->precision);
-  s->nc = q == 9 ? (f64 ? vlb::CoefLayout<9>::stride<double>() : vlb::CoefLayout<9>::stride<float>())
-                 : (f64 ? vlb::CoefLayout<19>::stride<double>() : vlb::CoefLayout<19>::stride<float>());
+  s->nc = q == 9    ? (f64 ? vlb::CoefLayout<9>::stride<double>() : vlb::CoefLayout<9>::stride<float>())
+          : q == 19 ? (f64 ? vlb::CoefLayout<19>::stride<double>() : vlb::CoefLayout<19>::stride<float>())
+                    : 0;  // D3Q39: no records, the kernels read the mesh geometry
+  if (q == VLB_D3Q39) s->ncoef = 0;
   const size_t es = f64 ? 8 : 4;
   // 16 bytes of padding: a 16-bit population is read as the aligned 32-bit
   // word that contains it
   cudaError_t e = cudaMalloc(&s->d_f, vlb::storage_bytes(params->precision) * q * mesh->ncell + 16);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_coef, es * s->nc * s->ncoef);
+  if (e == cudaSuccess && s->ncoef > 0) e = cudaMalloc(&s->d_coef, es * s->nc * s->ncoef);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
   if (e != cudaSuccess) {
     vlb_destroy(s);
     return fail(VLB_ENOMEM, "simulation device allocation: %s", cudaGetErrorString(e));
   }
-  e = vlb::launch_pack_coef(s, s->stream);
+  e = q == VLB_D3Q39 ? cudaSuccess : vlb::launch_pack_coef(s, s->stream);
   if (e != cudaSuccess) {
     vlb_destroy(s);
     return fail(VLB_ECUDA, "coefficient pack: %s", cudaGetErrorString(e));
@@ -334,7 +354,8 @@ int vlb_step(vlb_sim *s, int64_t nsteps) {
   if (!s) return fail(VLB_EINVAL, "NULL sim");
   if (nsteps < 0) return fail(VLB_EINVAL, "nsteps < 0");
   for (int64_t k = 0; k < nsteps; k++) {
-    cudaError_t e = vlb::launch_step(s, (int)(s->t & 1), s->stream);
+    cudaError_t e = s->mesh->md.q == VLB_D3Q39 ? vlb::q39_step(s, (int)(s->t & 1), s->stream)
+                                               : vlb::launch_step(s, (int)(s->t & 1), s->stream);
     if (e != cudaSuccess) return fail(VLB_ECUDA, "step launch: %s", cudaGetErrorString(e));
     s->t++;
   }
@@ -357,7 +378,8 @@ int vlb_moments(vlb_sim *s, double *rho, double *u, double *u_tilde, double *tot
     CU(cudaMalloc(&s->d_partial, sizeof(double) * 7 * 4 * 152));
     CU(cudaMalloc(&s->d_totals, sizeof(double) * 7));
   }
-  CU(vlb::launch_moments(s, s->d_fields, s->d_partial, nblk, s->stream));
+  CU(m->md.q == VLB_D3Q39 ? vlb::q39_moments(s, s->d_fields, s->d_partial, nblk, s->stream)
+                          : vlb::launch_moments(s, s->d_fields, s->d_partial, nblk, s->stream));
   CU(vlb::launch_finish_totals(s->d_partial, nblk, s->d_totals, s->stream));
   int rc = check_kernel_flags(s->d_err, s->stream);
   if (rc) return rc;
@@ -386,7 +408,7 @@ int vlb_get_state(vlb_sim *s, double *N) {
   const int q = s->mesh->md.q;
   int rc = ensure_io(s, sizeof(double) * nc * q);
   if (rc) return rc;
-  CU(vlb::launch_get_state(s, s->d_io, s->stream));
+  CU(q == VLB_D3Q39 ? vlb::q39_get_state(s, s->d_io, s->stream) : vlb::launch_get_state(s, s->d_io, s->stream));
   rc = check_kernel_flags(s->d_err, s->stream);
   if (rc) return rc;
   CU(cudaMemcpy(N, s->d_io, sizeof(double) * nc * q, cudaMemcpyDeviceToHost));
@@ -400,7 +422,7 @@ int vlb_set_state(vlb_sim *s, const double *N) {
   int rc = ensure_io(s, sizeof(double) * nc * q);
   if (rc) return rc;
   CU(cudaMemcpyAsync(s->d_io, N, sizeof(double) * nc * q, cudaMemcpyHostToDevice, s->stream));
-  CU(vlb::launch_set_state(s, s->d_io, s->stream));
+  CU(q == VLB_D3Q39 ? vlb::q39_set_state(s, s->d_io, s->stream) : vlb::launch_set_state(s, s->d_io, s->stream));
   CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
   CU(cudaStreamSynchronize(s->stream));
   s->t = 0;

@@ -175,6 +175,8 @@ int vlb_batch_create(vlb_sim *const *sims, int32_t nsims, vlb_batch **out) {
   if (!s0) return vlb::set_error(VLB_EINVAL, "vlb_batch_create: NULL simulation");
   if (s0->p.precision != VLB_F32 && s0->p.precision != VLB_F64)
     return vlb::set_error(VLB_EINVAL, "vlb_batch_create: batches take VLB_F32 or VLB_F64 members");
+  if (s0->mesh->md.q != VLB_D2Q9 && s0->mesh->md.q != VLB_D3Q19)
+    return vlb::set_error(VLB_EINVAL, "vlb_batch_create: batches take D2Q9 or D3Q19 members");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return vlb::set_error(VLB_ECUDA, "vlb_batch_create: no device");
   for (int32_t i = 0; i < nsims; i++) {

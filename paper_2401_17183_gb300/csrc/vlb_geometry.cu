@@ -3,6 +3,7 @@
 // and the equilibrium initialisation of the populations.
 #include "vlb_addr.cuh"
 #include "vlb_collide.cuh"
+#include "vlb_q39.cuh"
 
 namespace vlb {
 
@@ -213,6 +214,9 @@ cudaError_t launch_geometry(const vlb_mesh *m, int *d_err, cudaStream_t s) {
   if (m->md.q == 9)
     k_geometry<9><<<(unsigned)blocks, threads, 0, s>>>(m->md, g, m->ncell, m->d_J, m->d_gl,
                                                        m->d_gu, m->d_ginv, m->d_K, d_err);
+  else if (m->md.q == 39)
+    k_geometry<39><<<(unsigned)blocks, threads, 0, s>>>(m->md, g, m->ncell, m->d_J, m->d_gl,
+                                                        m->d_gu, m->d_ginv, m->d_K, d_err);
   else
     k_geometry<19><<<(unsigned)blocks, threads, 0, s>>>(m->md, g, m->ncell, m->d_J, m->d_gl,
                                                         m->d_gu, m->d_ginv, m->d_K, d_err);

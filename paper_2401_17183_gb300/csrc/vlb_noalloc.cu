@@ -189,6 +189,8 @@ cudaError_t launch_na(const vlb_sim *sim, double *scratch, int64_t nblk, double 
 extern "C" int vlb_totals_noalloc(vlb_sim *sim, double *d_totals) {
   if (!sim || !d_totals) return vlb::set_error(VLB_EINVAL, "vlb_totals_noalloc: NULL argument");
   const vlb_mesh *m = sim->mesh;
+  if (m->md.q != VLB_D2Q9 && m->md.q != VLB_D3Q19)
+    return vlb::set_error(VLB_EINVAL, "vlb_totals_noalloc: D2Q9 and D3Q19 only; use vlb_moments");
   const int64_t nblk = (m->ncell + vlb::kNaCellsPerBlock - 1) / vlb::kNaCellsPerBlock;
   if (nblk > vlb::kNaMaxBlocks)
     return vlb::set_error(VLB_EINVAL,

@@ -1,0 +1,425 @@
+// vlb_q39.cu -- the time step, initialisation, moments and state access for the
+// 6th-order isotropic D3Q39 velocity set (vlb_q39.cuh) on periodic meshes, in
+// FP64. The reduced force map of the D3Q19/D2Q9 kernels relies on velocity
+// components in {-1, 0, 1}; here every relation of section 2.2 is evaluated
+// direction by direction instead:
+//   f = N / J, rho and U (Eqs. 14, 15, 17); a fixed point on F (Eq. 27), each
+//   evaluation forming U~ = U + F / (2 rho), f^eq (Eq. 33 with T0 = 2/3),
+//   deltaPi (Eq. 30), deltaN (Eq. 31), Omega = -(N - J f^eq) / tau (Eq. 20)
+//   and N' = N + Omega + deltaN (Eq. 12); the converged N' is advected one to
+//   one (Eq. 22) in place with the A-A pattern of the other kernels (even
+//   steps: slot a of q in, slot abar of q out; odd steps: slot abar of q - c_a
+//   in, slot a of q + c_a out), with neighbours wrapped periodically on every
+//   axis (each axis at least 3 cells long, speeds at most 3).
+// The link coefficients K^i_a = sum_j c^j_a Theta^i_j(q + c_a, q) (Eq. 11)
+// come from the mesh's FP64 geometry, so the relations of Eqs. 27 and 30 read
+//   sum_j c^j_a Theta^i_j(q - c_a, q) = -K^i_abar.
+#include "vlb_addr.cuh"
+#include "vlb_q39.cuh"
+
+namespace vlb {
+namespace {
+
+constexpr int kQ39 = 39, kH39 = 19;
+constexpr int kQ39Threads = 128;
+
+struct Q39Args {
+  double *f;  // populations [39][ncell]
+  int64_t ncell;
+  int64_t n[3];
+  const double *J, *gl, *gu, *ginv, *K;
+  double body[3];
+  double tau, tol;
+  int32_t max_iter;
+  int *err;
+};
+
+__device__ __forceinline__ int opp39(int a) { return a == 0 ? 0 : (a <= kH39 ? a + kH39 : a - kH39); }
+
+__device__ __forceinline__ int64_t wrap(int64_t i, int64_t n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// cell index of q + s c_a (periodic on every axis; |c| <= 3 <= n)
+__device__ __forceinline__ int64_t nb39(const Q39Args &A, const int64_t ic[3], int a, int s) {
+  const int64_t i0 = wrap(ic[0] + s * Lat<39>::c(a, 0), A.n[0]);
+  const int64_t i1 = wrap(ic[1] + s * Lat<39>::c(a, 1), A.n[1]);
+  const int64_t i2 = wrap(ic[2] + s * Lat<39>::c(a, 2), A.n[2]);
+  return (i0 * A.n[1] + i1) * A.n[2] + i2;
+}
+
+__device__ __forceinline__ void coords(const Q39Args &A, int64_t c, int64_t ic[3]) {
+  ic[2] = c % A.n[2];
+  const int64_t r = c / A.n[2];
+  ic[1] = r % A.n[1];
+  ic[0] = r / A.n[1];
+}
+
+// storage location of the arrived population N_a(q) (A-A)
+template <bool ODD>
+__device__ __forceinline__ int64_t src39(const Q39Args &A, int64_t c, const int64_t ic[3], int a) {
+  if (!ODD || a == 0) return (int64_t)a * A.ncell + c;
+  return (int64_t)opp39(a) * A.ncell + nb39(A, ic, a, -1);
+}
+// storage location that receives N'_a(q)
+template <bool ODD>
+__device__ __forceinline__ int64_t dst39(const Q39Args &A, int64_t c, const int64_t ic[3], int a) {
+  if (!ODD) return (int64_t)opp39(a) * A.ncell + c;
+  if (a == 0) return c;
+  return (int64_t)a * A.ncell + nb39(A, ic, a, +1);
+}
+
+// g^ij - delta^ij of a cell (full 3 x 3) and G^i = G . g^i
+__device__ void cell_metric(const Q39Args &A, int64_t c, double gd[3][3], double G[3]) {
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) gd[i][j] = A.ginv[c * 6 + sym<3>(i, j)] - (i == j ? 1.0 : 0.0);
+  for (int i = 0; i < 3; i++) {
+    double s = 0.0;
+    for (int d = 0; d < 3; d++) s += A.body[d] * A.gu[(c * 3 + i) * 3 + d];
+    G[i] = s;
+  }
+}
+
+// Eq. 33 for every direction, with B^ij = (g^ij - delta^ij) T0 + U~^i U~^j and
+// C^ijk = T0 [(g^ij U~^k - delta^ij U^k) + cyclic] + U~^i U~^j U~^k:
+//   f^eq_a = rho w_a {1 + c.U / T0 + (c.B.c / T0 - tr B) / (2 T0)
+//                     + (C:ccc - 3 T0 c.V) / (6 T0^3)},  V^i = C^ijj
+__device__ void feq39(double rho, const double U[3], const double Ut[3], const double gd[3][3],
+                      double f[kQ39]) {
+  const double T0 = kT0_39;
+  double B[3][3], C[3][3][3], V[3];
+  double trB = 0.0;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) B[i][j] = gd[i][j] * T0 + Ut[i] * Ut[j];
+  for (int i = 0; i < 3; i++) trB += B[i][i];
+  // g^ij U~^k - delta^ij U^k = gd^ij U~^k + delta^ij (U~^k - U^k)
+  auto term = [&](int i, int j, int k) { return gd[i][j] * Ut[k] + (i == j ? Ut[k] - U[k] : 0.0); };
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++)
+      for (int k = 0; k < 3; k++)
+        C[i][j][k] = T0 * (term(i, j, k) + term(j, k, i) + term(k, i, j)) + Ut[i] * Ut[j] * Ut[k];
+  for (int i = 0; i < 3; i++) V[i] = C[i][0][0] + C[i][1][1] + C[i][2][2];
+#pragma unroll 1
+  for (int a = 0; a < kQ39; a++) {
+    const double c0 = Lat<39>::c(a, 0), c1 = Lat<39>::c(a, 1), c2 = Lat<39>::c(a, 2);
+    const double cv[3] = {c0, c1, c2};
+    double cu = 0.0, cBc = 0.0, cCc = 0.0, cV = 0.0;
+    for (int i = 0; i < 3; i++) {
+      cu += cv[i] * U[i];
+      cV += cv[i] * V[i];
+      for (int j = 0; j < 3; j++) {
+        cBc += cv[i] * cv[j] * B[i][j];
+        for (int k = 0; k < 3; k++) cCc += cv[i] * cv[j] * cv[k] * C[i][j][k];
+      }
+    }
+    const double s = 1.0 + cu / T0 + (cBc / T0 - trB) / (2.0 * T0) + (cCc - 3.0 * T0 * cV) / (6.0 * T0 * T0 * T0);
+    f[a] = rho * q39_w(a) * s;
+  }
+}
+
+// One evaluation of the collision at force F (Eqs. 20, 27, 30, 31, 33):
+// post-collision N' and the updated F.
+__device__ void eval39(const double N[kQ39], double J, double rho, const double U[3], const double F[3],
+                       const double gd[3][3], const double G[3], const double *K, double tau,
+                       double Np[kQ39], double Fn[3]) {
+  const double T0 = kT0_39;
+  double Ut[3], feq[kQ39];
+  for (int i = 0; i < 3; i++) Ut[i] = U[i] + 0.5 * (F[i] / rho);
+  feq39(rho, U, Ut, gd, feq);
+  // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a + K^j_abar) f^eq_a   (Eq. 30)
+  double dP[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll 1
+  for (int a = 1; a < kQ39; a++) {
+    const int ab = opp39(a);
+    for (int i = 0; i < 3; i++) {
+      const int ci = Lat<39>::c(a, i);
+      if (ci == 0) continue;
+      for (int j = 0; j < 3; j++) dP[i][j] += ci * (K[a * 3 + j] + K[ab * 3 + j]) * feq[a];
+    }
+  }
+  const double cp = -0.5 * (1.0 - 1.0 / (2.0 * tau));
+  double tr = 0.0;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) dP[i][j] *= cp;
+  for (int i = 0; i < 3; i++) tr += dP[i][i];
+  // deltaN_a = w_a J [c.F / T0 + (c.deltaPi.c / T0 - tr deltaPi) / T0]   (Eq. 31)
+  // N'_a = N_a - (N_a - J f^eq_a) / tau + deltaN_a   (Eqs. 12, 20)
+#pragma unroll 1
+  for (int a = 0; a < kQ39; a++) {
+    const double cv[3] = {(double)Lat<39>::c(a, 0), (double)Lat<39>::c(a, 1), (double)Lat<39>::c(a, 2)};
+    double cF = 0.0, cPc = 0.0;
+    for (int i = 0; i < 3; i++) {
+      cF += cv[i] * F[i];
+      for (int j = 0; j < 3; j++) cPc += cv[i] * cv[j] * dP[i][j];
+    }
+    const double dN = q39_w(a) * J * (cF / T0 + (cPc / T0 - tr) / T0);
+    Np[a] = N[a] - (N[a] - J * feq[a]) / tau + dN;
+  }
+  // J F^i = -1/2 sum_a (K^i_a N'_a + K^i_abar N_a) + J rho G^i   (Eq. 27 and the body force)
+  for (int i = 0; i < 3; i++) {
+    double s = 0.0;
+    for (int a = 1; a < kQ39; a++) s += K[a * 3 + i] * Np[a] + K[opp39(a) * 3 + i] * N[a];
+    Fn[i] = -0.5 * s / J + rho * G[i];
+  }
+}
+
+// The local fixed point on F from F = 0: converged when the change is at most
+// tol max(rho, |F|); N' at the converged F. False if max_iter is reached.
+__device__ bool collide39(const double N[kQ39], double J, const double gd[3][3], const double G[3],
+                          const double *K, double tau, double tol, int max_iter, double Np[kQ39],
+                          double &rho, double U[3], double F[3]) {
+  rho = 0.0;
+  for (int a = 0; a < kQ39; a++) rho += N[a] / J;
+  for (int i = 0; i < 3; i++) {
+    double s = 0.0;
+    for (int a = 0; a < kQ39; a++) s += Lat<39>::c(a, i) * (N[a] / J);
+    U[i] = s / rho;
+    F[i] = 0.0;
+  }
+  bool conv = false;
+  double Fn[3];
+  for (int it = 0; it < max_iter; it++) {
+    eval39(N, J, rho, U, F, gd, G, K, tau, Np, Fn);
+    double diff = 0.0, fmax = 0.0;
+    for (int i = 0; i < 3; i++) {
+      diff = maxnan(diff, fabs(Fn[i] - F[i]));
+      fmax = maxnan(fmax, fabs(Fn[i]));
+      F[i] = Fn[i];
+    }
+    if (diff <= tol * (rho > fmax ? rho : fmax)) {
+      conv = true;
+      break;
+    }
+  }
+  eval39(N, J, rho, U, F, gd, G, K, tau, Np, Fn);
+  return conv;
+}
+
+template <bool ODD>
+__global__ void __launch_bounds__(kQ39Threads) k_step39(const Q39Args A) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t ic[3];
+    coords(A, c, ic);
+    double N[kQ39], Np[kQ39];
+#pragma unroll 1
+    for (int a = 0; a < kQ39; a++) N[a] = A.f[src39<ODD>(A, c, ic, a)];
+    double gd[3][3], G[3], rho, U[3], F[3];
+    cell_metric(A, c, gd, G);
+    if (!collide39(N, A.J[c], gd, G, A.K + c * kQ39 * 3, A.tau, A.tol, A.max_iter, Np, rho, U, F))
+      atomicOr(A.err, ERR_NOCONV);
+#pragma unroll 1
+    for (int a = 0; a < kQ39; a++) A.f[dst39<ODD>(A, c, ic, a)] = Np[a];
+  }
+}
+
+__global__ void __launch_bounds__(kQ39Threads) k_init39(const Q39Args A, const double *rho, const double *u) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double gd[3][3], G[3], U[3], f[kQ39];
+    cell_metric(A, c, gd, G);
+    for (int i = 0; i < 3; i++) {
+      double s = 0.0;
+      for (int d = 0; d < 3; d++) s += u[c * 3 + d] * A.gu[(c * 3 + i) * 3 + d];  // U^i = u . g^i
+      U[i] = s;
+    }
+    feq39(rho[c], U, U, gd, f);
+    const double J = A.J[c];
+    for (int a = 0; a < kQ39; a++) A.f[(int64_t)a * A.ncell + c] = J * f[a];
+  }
+}
+
+__device__ __forceinline__ double warp_sum39(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// rho [ncell], u [ncell][3], u~ [ncell][3] into out; per-block conservation
+// sums (mass, P = sum e_a N_a, M = sum 1/2 [e_a(q) + e_a(q - c_a)] N_a) into
+// partial[block][7]
+template <bool ODD>
+__global__ void __launch_bounds__(kMomThreads) k_moments39(const Q39Args A, double *out, double *partial) {
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t ic[3];
+    coords(A, c, ic);
+    double N[kQ39], Np[kQ39];
+#pragma unroll 1
+    for (int a = 0; a < kQ39; a++) N[a] = A.f[src39<ODD>(A, c, ic, a)];
+    double gd[3][3], G[3], rho, U[3], F[3];
+    cell_metric(A, c, gd, G);
+    if (!collide39(N, A.J[c], gd, G, A.K + c * kQ39 * 3, A.tau, A.tol, A.max_iter, Np, rho, U, F))
+      atomicOr(A.err, ERR_NOCONV);
+    const double *gl = A.gl + c * 9;
+    out[c] = rho;
+    bool finite = isfinite(rho);
+    for (int d = 0; d < 3; d++) {
+      double uu = 0.0, ut = 0.0;
+      for (int i = 0; i < 3; i++) {
+        uu += U[i] * gl[i * 3 + d];                          // u = U^i g_i (Eq. 34)
+        ut += (U[i] + 0.5 * (F[i] / rho)) * gl[i * 3 + d];   // u~ = U~^i g_i
+      }
+      out[A.ncell + c * 3 + d] = uu;
+      out[A.ncell * 4 + c * 3 + d] = ut;
+      finite = finite && isfinite(uu) && isfinite(ut);
+    }
+    if (!finite) atomicOr(A.err, ERR_NONFINITE);
+#pragma unroll 1
+    for (int a = 0; a < kQ39; a++) {
+      acc[0] += N[a];
+      const double *gb = A.gl + nb39(A, ic, a, -1) * 9;
+      for (int d = 0; d < 3; d++) {
+        double e = 0.0, eb = 0.0;
+        for (int i = 0; i < 3; i++) {
+          e += Lat<39>::c(a, i) * gl[i * 3 + d];
+          eb += Lat<39>::c(a, i) * gb[i * 3 + d];
+        }
+        acc[1 + d] += e * N[a];
+        acc[4 + d] += 0.5 * (e + eb) * N[a];
+      }
+    }
+  }
+  __shared__ double sh[7][kMomThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 7; k++) {
+    const double s = warp_sum39(acc[k]);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < 7; k++) {
+      double s = lane < (int)(blockDim.x >> 5) ? sh[k][lane] : 0.0;
+      s = warp_sum39(s);
+      if (lane == 0) partial[(int64_t)blockIdx.x * 7 + k] = s;
+    }
+  }
+}
+
+template <bool ODD>
+__global__ void k_get39(const Q39Args A, double *N_out) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t ic[3];
+    coords(A, c, ic);
+    for (int a = 0; a < kQ39; a++) N_out[(int64_t)a * A.ncell + c] = A.f[src39<ODD>(A, c, ic, a)];
+  }
+}
+
+template <bool ODD>
+__global__ void k_set39(const Q39Args A, const double *N_in) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t ic[3];
+    coords(A, c, ic);
+    for (int a = 0; a < kQ39; a++) A.f[src39<ODD>(A, c, ic, a)] = N_in[(int64_t)a * A.ncell + c];
+  }
+}
+
+// per block: [min J, -max J, min f^eq_rest / w, min g^ii, -max g^ii]
+__global__ void __launch_bounds__(kStatThreads) k_stats39(const double *J, const double *ginv, int64_t ncell,
+                                                         double *partial) {
+  double v[5] = {1e300, 1e300, 1e300, 1e300, 1e300};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double gd[3][3], U0[3] = {0, 0, 0}, f[kQ39];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) gd[i][j] = ginv[c * 6 + sym<3>(i, j)] - (i == j ? 1.0 : 0.0);
+    feq39(1.0, U0, U0, gd, f);
+    v[0] = fmin(v[0], J[c]);
+    v[1] = fmin(v[1], -J[c]);
+    for (int a = 0; a < kQ39; a++) v[2] = fmin(v[2], f[a] / q39_w(a));
+    for (int i = 0; i < 3; i++) {
+      const double g = ginv[c * 6 + sym<3>(i, i)];
+      v[3] = fmin(v[3], g);
+      v[4] = fmin(v[4], -g);
+    }
+  }
+  __shared__ double sh[5][kStatThreads];
+  for (int k = 0; k < 5; k++) sh[k][threadIdx.x] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 5; k++) {
+      double m = sh[k][0];
+      for (int t = 1; t < (int)blockDim.x; t++) m = fmin(m, sh[k][t]);
+      partial[(int64_t)blockIdx.x * 5 + k] = m;
+    }
+  }
+}
+
+Q39Args make_args(const vlb_sim *sim) {
+  const vlb_mesh *m = sim->mesh;
+  Q39Args A;
+  A.f = static_cast<double *>(sim->d_f);
+  A.ncell = m->ncell;
+  for (int d = 0; d < 3; d++) {
+    A.n[d] = m->md.n[d];
+    A.body[d] = sim->p.body_force[d];
+  }
+  A.J = m->d_J;
+  A.gl = m->d_gl;
+  A.gu = m->d_gu;
+  A.ginv = m->d_ginv;
+  A.K = m->d_K;
+  A.tau = sim->p.tau;
+  A.tol = sim->p.tol;
+  A.max_iter = sim->p.max_iter;
+  A.err = sim->d_err;
+  return A;
+}
+
+unsigned grid_for(int64_t ncell, int threads) {
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (ncell + threads - 1) / threads;
+  const int64_t cap = (int64_t)nsm * 16;
+  return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t q39_mesh_stats(const vlb_mesh *m, double *d_partial, int64_t nblk, cudaStream_t s) {
+  k_stats39<<<(unsigned)nblk, kStatThreads, 0, s>>>(m->d_J, m->d_ginv, m->ncell, d_partial);
+  return cudaGetLastError();
+}
+
+cudaError_t q39_init(const vlb_sim *sim, const double *d_rho, const double *d_u, cudaStream_t s) {
+  const Q39Args A = make_args(sim);
+  k_init39<<<grid_for(A.ncell, kQ39Threads), kQ39Threads, 0, s>>>(A, d_rho, d_u);
+  return cudaGetLastError();
+}
+
+cudaError_t q39_step(const vlb_sim *sim, int odd, cudaStream_t s) {
+  const Q39Args A = make_args(sim);
+  if (odd)
+    k_step39<true><<<grid_for(A.ncell, kQ39Threads), kQ39Threads, 0, s>>>(A);
+  else
+    k_step39<false><<<grid_for(A.ncell, kQ39Threads), kQ39Threads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t q39_moments(const vlb_sim *sim, double *d_out, double *d_partial, int64_t nblk, cudaStream_t s) {
+  const Q39Args A = make_args(sim);
+  if (sim->t & 1)
+    k_moments39<true><<<(unsigned)nblk, kMomThreads, 0, s>>>(A, d_out, d_partial);
+  else
+    k_moments39<false><<<(unsigned)nblk, kMomThreads, 0, s>>>(A, d_out, d_partial);
+  return cudaGetLastError();
+}
+
+cudaError_t q39_get_state(const vlb_sim *sim, double *d_N, cudaStream_t s) {
+  const Q39Args A = make_args(sim);
+  if (sim->t & 1)
+    k_get39<true><<<grid_for(A.ncell, kQ39Threads), kQ39Threads, 0, s>>>(A, d_N);
+  else
+    k_get39<false><<<grid_for(A.ncell, kQ39Threads), kQ39Threads, 0, s>>>(A, d_N);
+  return cudaGetLastError();
+}
+
+// written in the layout of time 0 (even), which the caller then sets
+cudaError_t q39_set_state(const vlb_sim *sim, const double *d_N, cudaStream_t s) {
+  const Q39Args A = make_args(sim);
+  k_set39<false><<<grid_for(A.ncell, kQ39Threads), kQ39Threads, 0, s>>>(A, d_N);
+  return cudaGetLastError();
+}
+
+}  // namespace vlb

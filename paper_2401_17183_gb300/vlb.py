@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvlb.so")
 
 VLB_OK, VLB_EINVAL, VLB_EGEOM, VLB_ENOCONV, VLB_ENOMEM, VLB_ECUDA, VLB_ENONFINITE = range(7)
-VLB_D2Q9, VLB_D3Q19 = 9, 19
+VLB_D2Q9, VLB_D3Q19, VLB_D3Q39 = 9, 19, 39
 VLB_PERIODIC, VLB_WALL = 0, 1
 VLB_F64, VLB_F32, VLB_F16, VLB_BF16 = 0, 1, 2, 3
 VLB_REF_UNIFORM, VLB_REF_REST = 0, 1
