@@ -23,6 +23,22 @@ namespace {
 constexpr int kQ39 = 39, kH39 = 19;
 constexpr int kQ39Threads = 128;
 
+// the velocity set and weights as a table in constant memory: the direction
+// loops below are not unrolled, and a warp reads one entry at a time
+struct Q39Table {
+  double c[kQ39][3];
+  double w[kQ39];
+};
+constexpr Q39Table make_q39_table() {
+  Q39Table t{};
+  for (int a = 0; a < kQ39; a++) {
+    for (int d = 0; d < 3; d++) t.c[a][d] = Lat<39>::c(a, d);
+    t.w[a] = q39_w(a);
+  }
+  return t;
+}
+__constant__ Q39Table kT39 = make_q39_table();
+
 struct Q39Args {
   double *f;  // populations [39][ncell]
   int64_t ncell;
@@ -97,21 +113,21 @@ __device__ void feq39(double rho, const double U[3], const double Ut[3], const d
       for (int k = 0; k < 3; k++)
         C[i][j][k] = T0 * (term(i, j, k) + term(j, k, i) + term(k, i, j)) + Ut[i] * Ut[j] * Ut[k];
   for (int i = 0; i < 3; i++) V[i] = C[i][0][0] + C[i][1][1] + C[i][2][2];
+  // the symmetric contractions over their distinct components (B and C are
+  // symmetric): c.B.c from 6 terms, C:ccc from 10
 #pragma unroll 1
   for (int a = 0; a < kQ39; a++) {
-    const double c0 = Lat<39>::c(a, 0), c1 = Lat<39>::c(a, 1), c2 = Lat<39>::c(a, 2);
-    const double cv[3] = {c0, c1, c2};
-    double cu = 0.0, cBc = 0.0, cCc = 0.0, cV = 0.0;
-    for (int i = 0; i < 3; i++) {
-      cu += cv[i] * U[i];
-      cV += cv[i] * V[i];
-      for (int j = 0; j < 3; j++) {
-        cBc += cv[i] * cv[j] * B[i][j];
-        for (int k = 0; k < 3; k++) cCc += cv[i] * cv[j] * cv[k] * C[i][j][k];
-      }
-    }
+    const double x = kT39.c[a][0], y = kT39.c[a][1], z = kT39.c[a][2];
+    const double cu = x * U[0] + y * U[1] + z * U[2];
+    const double cV = x * V[0] + y * V[1] + z * V[2];
+    const double cBc = x * x * B[0][0] + y * y * B[1][1] + z * z * B[2][2] +
+                       2.0 * (x * y * B[0][1] + x * z * B[0][2] + y * z * B[1][2]);
+    const double cCc = x * x * x * C[0][0][0] + y * y * y * C[1][1][1] + z * z * z * C[2][2][2] +
+                       3.0 * (x * x * y * C[0][0][1] + x * x * z * C[0][0][2] + y * y * x * C[1][1][0] +
+                              y * y * z * C[1][1][2] + z * z * x * C[2][2][0] + z * z * y * C[2][2][1]) +
+                       6.0 * x * y * z * C[0][1][2];
     const double s = 1.0 + cu / T0 + (cBc / T0 - trB) / (2.0 * T0) + (cCc - 3.0 * T0 * cV) / (6.0 * T0 * T0 * T0);
-    f[a] = rho * q39_w(a) * s;
+    f[a] = rho * kT39.w[a] * s;
   }
 }
 
@@ -130,8 +146,7 @@ __device__ void eval39(const double N[kQ39], double J, double rho, const double 
   for (int a = 1; a < kQ39; a++) {
     const int ab = opp39(a);
     for (int i = 0; i < 3; i++) {
-      const int ci = Lat<39>::c(a, i);
-      if (ci == 0) continue;
+      const double ci = kT39.c[a][i];
       for (int j = 0; j < 3; j++) dP[i][j] += ci * (K[a * 3 + j] + K[ab * 3 + j]) * feq[a];
     }
   }
@@ -144,13 +159,13 @@ __device__ void eval39(const double N[kQ39], double J, double rho, const double 
   // N'_a = N_a - (N_a - J f^eq_a) / tau + deltaN_a   (Eqs. 12, 20)
 #pragma unroll 1
   for (int a = 0; a < kQ39; a++) {
-    const double cv[3] = {(double)Lat<39>::c(a, 0), (double)Lat<39>::c(a, 1), (double)Lat<39>::c(a, 2)};
+    const double cv[3] = {kT39.c[a][0], kT39.c[a][1], kT39.c[a][2]};
     double cF = 0.0, cPc = 0.0;
     for (int i = 0; i < 3; i++) {
       cF += cv[i] * F[i];
       for (int j = 0; j < 3; j++) cPc += cv[i] * cv[j] * dP[i][j];
     }
-    const double dN = q39_w(a) * J * (cF / T0 + (cPc / T0 - tr) / T0);
+    const double dN = kT39.w[a] * J * (cF / T0 + (cPc / T0 - tr) / T0);
     Np[a] = N[a] - (N[a] - J * feq[a]) / tau + dN;
   }
   // J F^i = -1/2 sum_a (K^i_a N'_a + K^i_abar N_a) + J rho G^i   (Eq. 27 and the body force)
@@ -170,7 +185,7 @@ __device__ bool collide39(const double N[kQ39], double J, const double gd[3][3],
   for (int a = 0; a < kQ39; a++) rho += N[a] / J;
   for (int i = 0; i < 3; i++) {
     double s = 0.0;
-    for (int a = 0; a < kQ39; a++) s += Lat<39>::c(a, i) * (N[a] / J);
+    for (int a = 0; a < kQ39; a++) s += kT39.c[a][i] * (N[a] / J);
     U[i] = s / rho;
     F[i] = 0.0;
   }
