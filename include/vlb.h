@@ -170,7 +170,8 @@ void vlb_mesh_destroy(vlb_mesh *mesh);
  * arrays (Euclidean velocity). The mesh must outlive the simulation.
  * Errors: VLB_EINVAL (tau <= 1/2, bad precision, coef_mode or reference,
  * VLB_REF_REST without plane mode, moving walls on a cell touching two
- * walls), VLB_ENOMEM, VLB_ECUDA. */
+ * walls, a D3Q39 mesh with a precision other than VLB_F64 or with
+ * VLB_COEF_PLANE), VLB_ENOMEM, VLB_ECUDA. */
 int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, const double *u,
              vlb_sim **out);
 /* Re-initialise the populations from host fields as vlb_init does (no allocation). */
@@ -221,7 +222,8 @@ const char *vlb_last_error(void);
  *           lattice, precision (VLB_F32 or VLB_F64), coefficient mode (all
  *           plane or all full), time parity and stream, each with fewer than
  *           2^31 / q cells; they must outlive the batch and are not copied
- * Errors: VLB_EINVAL (mismatch, 16-bit storage, NULL), VLB_ENOMEM, VLB_ECUDA. */
+ * Errors: VLB_EINVAL (mismatch, 16-bit storage, D3Q39 members, NULL),
+ * VLB_ENOMEM, VLB_ECUDA. */
 typedef struct vlb_batch vlb_batch;
 int vlb_batch_create(vlb_sim *const *sims, int32_t nsims, vlb_batch **out);
 /* Advance every member nsteps steps (asynchronous on the members' stream;
@@ -252,7 +254,8 @@ void vlb_batch_destroy(vlb_batch *b);
  * address; make the first call before any stream capture. All calls share the
  * array, so calls that overlap on the GPU (for example on two streams) race
  * and give wrong totals; every call writes each slot it reads before reading
- * it, so nothing needs clearing. Errors: VLB_EINVAL, VLB_ECUDA. Kernel-raised
+ * it, so nothing needs clearing. D2Q9 and D3Q19 simulations only (D3Q39:
+ * VLB_EINVAL, use vlb_moments). Errors: VLB_EINVAL, VLB_ECUDA. Kernel-raised
  * errors are not checked here (no synchronisation). */
 int vlb_totals_noalloc(vlb_sim *sim, double *d_totals);
 
