@@ -45,9 +45,10 @@ def test_binding_covers_the_header():
 def test_lattice_matches_paper_set_and_pairs():
     from oracle import lattice as olat
     from paper_2401_17183_gb300 import vlb
-    for q in (9, 19):
+    for q in (9, 19, 39):
         c, w = vlb.lattice(q)
         co, wo, _ = olat(q)
+        assert len({tuple(v) for v in c}) == q
         assert sorted(map(tuple, c)) == sorted(map(tuple, co))
         # weights agree direction by direction
         for a in range(q):
