@@ -388,6 +388,15 @@ def test_error_paths(V):
     s2 = V.Sim(good, W.params(0.8), rho, u)
     s2.step(2)
     s2.sync()
+    # a non-finite population, injected on the host through the state, is reported
+    s3 = V.Sim(good, W.params(0.8), rho, u)
+    N = s3.get_state()
+    N[3, 17] = np.nan
+    s3.set_state(N)
+    s3.step(1)
+    with pytest.raises(V.VlbError) as e:
+        s3.sync()
+    assert e.value.code in ("ENOCONV", "ENONFINITE")
 
 
 def test_64bit_offsets_match_tiled_short_mesh(V):
