@@ -12,6 +12,24 @@
 
 namespace {
 
+// The packed FP32 arithmetic of the step kernel loads coefficient pairs as
+// 8-byte values: every pair must start on an even element of a record whose
+// stride keeps 16-byte alignment.
+template <int Q>
+constexpr bool record_pairs_aligned() {
+  using L = vlb::CoefLayout<Q>;
+  constexpr int D = L::D;
+  bool ok = L::template stride<float>() % 4 == 0 && L::ROWN % 4 == 0;
+  for (int p = 1; p <= L::H; p++) ok = ok && L::mp(p, 0) % 2 == 0 && L::dk(p, 0) % 2 == 0;
+  for (int k = 0; k < L::NS; k++) ok = ok && L::row(L::PE, L::NS, 0, k) % 2 == 0;
+  for (int k = 0; k < L::NO; k++) ok = ok && L::row(L::PO2, L::NO, 0, k) % 2 == 0;
+  for (int k = 0; k < D; k++)
+    ok = ok && L::row(L::LO, D, 0, k) % 2 == 0 && L::row(L::TL, D, 0, k) % 2 == 0 &&
+         L::row(L::HM, D, 0, k) % 2 == 0;
+  return ok;
+}
+static_assert(record_pairs_aligned<9>() && record_pairs_aligned<19>(), "coefficient pairs must be 8-byte aligned");
+
 thread_local char g_err[512] = "";
 
 int fail(int code, const char *fmt, ...) {
