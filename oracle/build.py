@@ -13,17 +13,32 @@ SRC = os.path.join(HERE, "vlb_oracle.c")
 HDR = os.path.join(HERE, "vlb_oracle.h")
 
 
+def _cc(out, src):
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-Wall", "-fPIC", "-shared",
+           "-I", HERE, "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+
+
+def build_oracle_copy(source_text: str, out_dir: str) -> str:
+    """Compile a modified copy of the oracle source (tests that plant a
+    mistake in the oracle) into out_dir; returns the library path."""
+    src = os.path.join(out_dir, "vlb_oracle_copy.c")
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    out = os.path.join(out_dir, "liboracle_copy.so")
+    _cc(out, src)
+    return out
+
+
 def build_oracle(force: bool = False) -> str:
     """Build the oracle library if it is missing or older than its sources."""
     if not force and os.path.exists(LIB):
         lt = os.path.getmtime(LIB)
         if lt >= os.path.getmtime(SRC) and lt >= os.path.getmtime(HDR):
             return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-Wall", "-fPIC", "-shared",
-           "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    _cc(LIB, SRC)
     return LIB
 
 

@@ -53,31 +53,40 @@ def _check(rc, what):
         raise OracleError(rc, what)
 
 
+def _configure(lib):
+    dp = C.POINTER(C.c_double)
+    lib.vlbo_lattice.argtypes = [C.c_int32, C.POINTER(C.c_int32), dp, dp]
+    lib.vlbo_position.argtypes = [C.POINTER(_Mesh), C.POINTER(C.c_int64), dp]
+    lib.vlbo_cell_geometry.argtypes = [C.POINTER(_Mesh), C.POINTER(_Params),
+                                       C.POINTER(C.c_int64), C.POINTER(_Cell)]
+    lib.vlbo_equilibrium.argtypes = [C.c_int32, C.c_double, dp, dp, dp, dp]
+    lib.vlbo_collide.argtypes = [C.c_int32, C.POINTER(_Cell), C.POINTER(_Params), dp,
+                                 dp, dp, dp, dp, dp, dp, C.POINTER(C.c_int32)]
+    lib.vlbo_create.argtypes = [C.POINTER(_Mesh), C.POINTER(_Params), C.POINTER(C.c_void_p)]
+    lib.vlbo_destroy.argtypes = [C.c_void_p]
+    lib.vlbo_destroy.restype = None
+    lib.vlbo_init.argtypes = [C.c_void_p, dp, dp]
+    lib.vlbo_step.argtypes = [C.c_void_p, C.c_int64]
+    lib.vlbo_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
+    lib.vlbo_get_state.argtypes = [C.c_void_p, dp]
+    lib.vlbo_set_state.argtypes = [C.c_void_p, dp]
+    lib.vlbo_get_cell.argtypes = [C.c_void_p, C.c_int64, C.POINTER(_Cell)]
+    lib.vlbo_last_iters.argtypes = [C.c_void_p]
+    lib.vlbo_last_iters.restype = C.c_int32
+    return lib
+
+
 def load():
     global _lib
     if _lib is None:
-        lib = C.CDLL(build_oracle())
-        dp = C.POINTER(C.c_double)
-        lib.vlbo_lattice.argtypes = [C.c_int32, C.POINTER(C.c_int32), dp, dp]
-        lib.vlbo_position.argtypes = [C.POINTER(_Mesh), C.POINTER(C.c_int64), dp]
-        lib.vlbo_cell_geometry.argtypes = [C.POINTER(_Mesh), C.POINTER(_Params),
-                                           C.POINTER(C.c_int64), C.POINTER(_Cell)]
-        lib.vlbo_equilibrium.argtypes = [C.c_int32, C.c_double, dp, dp, dp, dp]
-        lib.vlbo_collide.argtypes = [C.c_int32, C.POINTER(_Cell), C.POINTER(_Params), dp,
-                                     dp, dp, dp, dp, dp, dp, C.POINTER(C.c_int32)]
-        lib.vlbo_create.argtypes = [C.POINTER(_Mesh), C.POINTER(_Params), C.POINTER(C.c_void_p)]
-        lib.vlbo_destroy.argtypes = [C.c_void_p]
-        lib.vlbo_destroy.restype = None
-        lib.vlbo_init.argtypes = [C.c_void_p, dp, dp]
-        lib.vlbo_step.argtypes = [C.c_void_p, C.c_int64]
-        lib.vlbo_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
-        lib.vlbo_get_state.argtypes = [C.c_void_p, dp]
-        lib.vlbo_set_state.argtypes = [C.c_void_p, dp]
-        lib.vlbo_get_cell.argtypes = [C.c_void_p, C.c_int64, C.POINTER(_Cell)]
-        lib.vlbo_last_iters.argtypes = [C.c_void_p]
-        lib.vlbo_last_iters.restype = C.c_int32
-        _lib = lib
+        _lib = _configure(C.CDLL(build_oracle()))
     return _lib
+
+
+def load_library(path):
+    """A separately built copy of the oracle (the tests build mutated copies
+    to show that a pin fails when the oracle is wrong)."""
+    return _configure(C.CDLL(path))
 
 
 def _dp(a):
@@ -203,8 +212,8 @@ def collide(q, cell, params, N):
 class OracleSim:
     """Whole-mesh FP64 simulation: geometry, init, step, moments."""
 
-    def __init__(self, mesh, params):
-        self.lib = load()
+    def __init__(self, mesh, params, lib=None):
+        self.lib = load() if lib is None else lib
         self.mesh = mesh
         self.q = int(mesh["q"])
         self.dim = int(mesh["dim"])
