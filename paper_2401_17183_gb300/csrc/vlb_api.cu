@@ -13,19 +13,20 @@
 namespace {
 
 // The packed FP32 arithmetic of the step kernel loads coefficient pairs as
-// 8-byte values: every pair must start on an even element of a record whose
-// stride keeps 16-byte alignment.
+// 8-byte values and quads as 16-byte values: every pair must start on an even
+// element and every quad on a multiple of four of a record whose stride keeps
+// 16-byte alignment.
 template <int Q>
 constexpr bool record_pairs_aligned() {
   using L = vlb::CoefLayout<Q>;
   constexpr int D = L::D;
-  bool ok = L::template stride<float>() % 4 == 0 && L::ROWN % 4 == 0;
-  for (int p = 1; p <= L::H; p++) ok = ok && L::mp(p, 0) % 2 == 0 && L::dk(p, 0) % 2 == 0;
-  for (int k = 0; k < L::NS; k++) ok = ok && L::row(L::PE, L::NS, 0, k) % 2 == 0;
-  for (int k = 0; k < L::NO; k++) ok = ok && L::row(L::PO2, L::NO, 0, k) % 2 == 0;
-  for (int k = 0; k < D; k++)
-    ok = ok && L::row(L::LO, D, 0, k) % 2 == 0 && L::row(L::TL, D, 0, k) % 2 == 0 &&
-         L::row(L::HM, D, 0, k) % 2 == 0;
+  bool ok = L::template stride<float>() % 4 == 0 && L::ROWN % 4 == 0 && L::MPD % 4 == 0 &&
+            L::QM % 4 == 0 && L::HM % 2 == 0;
+  // 16-byte quads of the link coefficients, 8-byte component-2 pairs
+  for (int p = 1; p <= L::H; p++) ok = ok && L::mp(p, 0) % 4 == 0 && (D == 2 || L::mp(p, 2) % 2 == 0);
+  // rows 0 and 1 of the chord step as 16-byte quads, row 2 likewise
+  ok = ok && (2 * L::NQ) % 2 == 0 && (D == 2 || (L::row(L::QM, L::NQ, 2, 0) % 4 == 0 && L::NQ % 4 == 0));
+  for (int k = 0; k < D; k++) ok = ok && L::row(L::HM, D, 0, k) % 2 == 0;
   return ok;
 }
 static_assert(record_pairs_aligned<9>() && record_pairs_aligned<19>(), "coefficient pairs must be 8-byte aligned");
@@ -307,8 +308,10 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
   if (s->p.max_iter <= 0) s->p.max_iter = 100;
   if (s->p.tol <= 0.0) s->p.tol = params->precision == VLB_F64 ? 1e-14 : 1e-6;
   s->stream = (cudaStream_t)params->stream;
-  // uniform storage reference n_ref = rho_0 J_ref, rho_0 = 1, J_ref mid-range of J
-  s->nref = 0.5 * (mesh->stats.J_min + mesh->stats.J_max);
+  // uniform storage reference n_ref = rho_0 J_ref, rho_0 = 1, J_ref mid-range of J,
+  // rounded to a value FP32 represents exactly, so that the FP32 step kernel
+  // and the FP64 kernels (initialisation, moments, state) use the same one
+  s->nref = (double)(float)(0.5 * (mesh->stats.J_min + mesh->stats.J_max));
   bool plane = false;
   if (params->coef_mode == VLB_COEF_PLANE) {
     if (!mesh->stats.invariant_fast_axis) {

@@ -348,8 +348,25 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
     }
     CollideState<Q, double> cs;
     // chord iteration from F = 0 (the record's FR is still zero here)
-    collide_cell<Q, double, true, false>(N, rec, 0.0, 1.0 / a.tau, 1e-15, 400, Np, cs);
+    collide_cell<Q, double, false>(N, rec, 0.0, 1.0 / a.tau, 1e-15, 400, Np, cs);
     for (int i = 0; i < D; i++) rec[L::FR + i] = cs.conv ? cs.F[i] : 0.0;
+  }
+  // the local rest state for the final pass: deviations from the uniform
+  // reference, their sum over all directions, and the rest weights
+  {
+    double gd[NS], U0[D], rsum = 0.0;
+    for (int i = 0; i < NS; i++) gd[i] = rec[L::GINV + i];
+    for (int i = 0; i < D; i++) U0[i] = 0.0;
+    EqParts<Q, double> e;
+    eq_parts<Q, double>(gd, U0, U0, e);
+    for (int p = 0; p <= H; p++) {
+      const double rwp = lat_w<Q, double>(p) * eq_even<Q, double>(e, p);
+      const double r = a.J[c] * rwp - lat_w<Q, double>(p) * a.nref;
+      rec[L::RR + p] = r;
+      rec[L::RW + p] = rwp;
+      rsum += p == 0 ? r : 2.0 * r;
+    }
+    rec[L::RR + H + 1] = rsum;
   }
   // storage references: the rest state of Eq. 33 at the column that holds each
   // location, as offsets from the uniform reference (the fastest axis never

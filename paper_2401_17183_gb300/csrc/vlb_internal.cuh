@@ -57,6 +57,18 @@ __host__ __device__ constexpr int lat_nnz(int a) {
   return (Lat<Q>::c(a, 0) != 0) + (Lat<Q>::c(a, 1) != 0) + (Lat<Q>::c(a, 2) != 0);
 }
 
+// the k-th non-zero component axis of c_a (k = 0, 1), or -1
+template <int Q>
+__host__ __device__ constexpr int nz_axis(int a, int k) {
+  int n = 0;
+  for (int i = 0; i < 3; i++)
+    if (Lat<Q>::c(a, i) != 0) {
+      if (n == k) return i;
+      n++;
+    }
+  return -1;
+}
+
 template <int Q, typename R>
 __host__ __device__ constexpr R lat_w(int a) {
   return Q == 9 ? (a == 0 ? R(4) / R(9) : lat_nnz<Q>(a) == 1 ? R(1) / R(9) : R(1) / R(36))
@@ -84,18 +96,21 @@ __host__ __device__ constexpr int offd(int k, int l) {
 // Coefficient record of one cell (or one column in plane mode). Records are
 // stored one after another (record r at coef + r * RS). Everything in a
 // record is a function of the cell geometry and tau alone, formed once in
-// FP64 and rounded to the storage type. The record falls into three groups,
-// each starting on a multiple of four elements (16 bytes or more), so that a
+// FP64 and rounded to the storage type. The record falls into groups, each
+// starting on a multiple of four elements (16 bytes or more), so that a
 // group can be read with vector loads: the set-up of a collision, the link
-// coefficients, and the coefficients of one evaluation of the map.
+// coefficients, the chord matrix and the coefficients of one evaluation of
+// the map.
 //
 // Link coefficients are stored per pair (p, pbar = p + H) as
 // am M_p and ad D_p with M_p = K_p + K_pbar, D_p = K_p - K_pbar and the weights
 // am = -(2 - 1/tau)/4, ad = (1/tau)/4 that they carry in the constant part
-// of the map (see collide_cell), interleaved pair by pair. The
-// last group holds the coefficients of the fixed-point map of Eq. 27 written
-// as a polynomial in U~ (see build_record), so that one evaluation of the map
-// costs a few dozen products instead of a pass over all directions.
+// of the map (see collide_cell): components 0 and 1 of pair p as one 16-byte
+// quad (am M^0, am M^1, ad D^0, ad D^1), then (D = 3) the component-2 pairs
+// (am M^2, ad D^2). The last group holds the coefficients of the fixed-point
+// map of Eq. 27 written as a polynomial in U~, premultiplied by the chord
+// matrix (see build_record), so that one chord step costs a few dozen products
+// instead of a pass over all directions.
 __host__ __device__ constexpr int round4(int n) { return (n + 3) / 4 * 4; }
 __host__ __device__ constexpr int round2(int n) { return (n + 1) / 2 * 2; }
 
@@ -104,44 +119,54 @@ struct CoefLayout {
   static constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   static constexpr int NS = D * (D + 1) / 2;   // symmetric pairs
   static constexpr int NO = D * (D - 1);       // ordered off-diagonal pairs
+  static constexpr int NQ = NS + NO;           // monomials of U~ in one chord step
   // set-up of a collision
   static constexpr int J = 0;                  // J (Eq. 5)
   static constexpr int GINV = 1;               // g^ij - delta^ij packed (Eq. 8)
-  static constexpr int BODY = GINV + NS;       // G^i = G . g^i
+  static constexpr int GH = GINV + NS;         // (g^ij - delta^ij) / 2 packed
+  static constexpr int BODY = GH + NS;         // G^i = G . g^i
   static constexpr int KW = BODY + D;          // sum_a w_a K^i_a (reference-state part of J F)
   static constexpr int KWL = KW + D;           // its low part: KW + KWL = the FP64 value
   static constexpr int FR = KWL + D;           // F of the rest state at rho = 1 (start value)
   static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
   static constexpr int CE = UW + D;            // constant term of the map
-  static constexpr int PO1 = CE + D;           // D x D: coefficient of U
+  static constexpr int PO1 = CE + D;           // D x D: coefficient of U (row-major)
   static constexpr int IJ = PO1 + D * D;       // 1 / J
-  // link coefficients, 2D per pair p: am M_p^0, am M_p^1, ad D_p^0, ad D_p^1,
-  // then (D = 3) am M_p^2, ad D_p^2 -- components 0 and 1 as 8-byte pairs
+  // link coefficients (see above)
   static constexpr int MPD = round4(IJ + 1);
-  // one evaluation of the map: blocks of D rows (component i of Phi) of n
-  // coefficients each, stored with rows 0 and 1 interleaved (k-th pair at
-  // base + 2k, 8-byte aligned, for packed FP32 arithmetic) and row 2 after
-  // them; every block starts on an even element (see row())
-  static constexpr int HM = round4(MPD + 2 * H * D);  // D x D chord matrix (I - L)^-1
-  static constexpr int PE = HM + round2(D * D);       // D x NS: coefficient of U~^k U~^l (k <= l)
-  static constexpr int PO2 = PE + round2(D * NS);     // D x NO: coefficient of (U~^k)^2 U~^l (k != l)
-  static constexpr int LO = PO2 + round2(D * NO);     // D x D: coefficient of U~
-  static constexpr int TL = LO + round2(D * D);       // D x D: coefficient of J F
+  // blocks of D rows (component i of Phi) of n coefficients each, stored with
+  // rows 0 and 1 interleaved (k-th pair at base + 2k, 8-byte aligned, for
+  // packed FP32 arithmetic) and row 2 after them (see row())
+  static constexpr int HM = round4(MPD + 2 * H * D);  // D x D: chord matrix (I - L)^-1 minus I
+  // H PE and H PO2 side by side: column s < NS is the coefficient of
+  // U~^k U~^l (s = sym(k, l)), column NS + offd(k, l) that of (U~^k)^2 U~^l
+  static constexpr int QM = round4(HM + round2(D * D));
   // element k of row i of the block that starts at base and has n per row
   __host__ __device__ static constexpr int row(int base, int n, int i, int k) {
     return i < 2 ? base + 2 * k + i : base + 2 * n + (i - 2) * n + k;
   }
+  // the local rest state (rho = 1, U = 0) of Eq. 33, for the final pass:
+  // RR + p (p = 0..H) its deviation from the uniform reference,
+  // J w_p (1 + x_p) - w_p n_ref (even in the direction), RR + H + 1 the sum of
+  // those deviations over all Q directions, and RW + p the weight of the rest
+  // state, w_p (1 + x_p)
+  static constexpr int RR = round4(QM + D * NQ);
+  static constexpr int RW = RR + round4(H + 2);
   // storage references of 16-bit populations (reference VLB_REF_REST, plane
   // mode), as offsets from the uniform reference, r - w_a n_ref: at the cell's
   // own locations, at the location each population of an odd step is read
   // from (slot abar of q - c_a), and at the one it is written to (slot a of
   // q + c_a); a link through a wall reads and writes the cell's own slot
-  static constexpr int ROWN = round4(TL + round2(D * D));
+  static constexpr int ROWN = round4(RW + H + 1);
   static constexpr int RIN = ROWN + Q;
   static constexpr int ROUT = RIN + Q;
   static constexpr int NC = ROUT + Q;
-  __host__ __device__ static constexpr int mp(int p, int i) { return MPD + (p - 1) * 2 * D + (i < 2 ? i : 4); }
-  __host__ __device__ static constexpr int dk(int p, int i) { return MPD + (p - 1) * 2 * D + (i < 2 ? 2 + i : 5); }
+  __host__ __device__ static constexpr int mp(int p, int i) {
+    return i < 2 ? MPD + 4 * (p - 1) + i : MPD + 4 * H + 2 * (p - 1);
+  }
+  __host__ __device__ static constexpr int dk(int p, int i) {
+    return i < 2 ? MPD + 4 * (p - 1) + 2 + i : MPD + 4 * H + 2 * (p - 1) + 1;
+  }
   // record stride in elements of type R: a multiple of four elements, so that
   // every record and group starts on a 16-byte boundary
   template <typename R>

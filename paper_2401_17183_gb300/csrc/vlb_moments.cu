@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const MomArgs a, double
     MT Np[Q];
     CollideState<Q, MT> st;
     // chord iteration from the record's rest-state start value
-    collide_cell<Q, MT, true, false>(dv, rec, static_cast<MT>(a.nref), static_cast<MT>(1.0 / a.tau),
+    collide_cell<Q, MT, false>(dv, rec, static_cast<MT>(a.nref), static_cast<MT>(1.0 / a.tau),
                                      static_cast<MT>(a.tol), 200, Np, st);
     if (!st.conv) atomicOr(a.err, ERR_NOCONV);
     double gl[D][D];

@@ -308,7 +308,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
       // ---- collide (section 2.2)
       R Np[Q];
       CollideState<Q, R> cst;
-      collide_cell<Q, R, true, true>(N, rc, arg_r<R>(a.nref, a.nref_f), arg_r<R>(a.itau, a.itau_f),
+      collide_cell<Q, R, true>(N, rc, arg_r<R>(a.nref, a.nref_f), arg_r<R>(a.itau, a.itau_f),
                                      arg_r<R>(a.tol, a.tol_f), a.max_iter, Np, cst);
       if (!cst.conv) atomicOr(a.err, ERR_NOCONV);
 

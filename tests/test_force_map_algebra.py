@@ -13,7 +13,11 @@ the blocks from the geometry (independently of the CUDA sources) and checks
   - that the reduced map equals the direct evaluation of Eqs. 27/30/31/33 for
     arbitrary Phi, populations and geometry (D2Q9 and D3Q19);
   - that the chord iteration with H = (I + LO/4 + TL/2)^-1 converges to the
-    oracle's F.
+    oracle's F;
+  - that the chord step the kernel takes, Phi <- H (Pc - 1/2 m Q(U~)) with
+    Pc = Pb' - 1/2 m LO U and Q = PE : U~U~ + PO2 : (U~^k)^2 U~^l (the linear
+    part of the map cancels against H exactly), equals Phi + H (map(Phi) - Phi)
+    computed from the direct evaluation, and reaches the oracle's F.
 
 A wrong sign, a dropped term or a transposed index in the derivation fails
 the first check by many orders of magnitude above round-off.
@@ -95,6 +99,17 @@ def _maps(q, g, tau, N, G):
         return m * G - 0.5 * K.T @ Np + 0.5 * L.T @ N
 
     H = np.linalg.inv(np.eye(D) + 0.25 * b['LO'] + 0.5 * b['TL'])
+
+    def folded(Phi):
+        """One chord step in the form the CUDA collision evaluates it."""
+        Ut = U + Phi / (2 * m)
+        cub = sum(b['PO2'][:, k, l] * Ut[k] ** 2 * Ut[l]
+                  for k in range(D) for l in range(D) if k != l)
+        Qn = np.einsum('ikl,k,l->i', b['PE'], Ut, Ut) + cub
+        Pc = Pb - 0.5 * m * (b['LO'] @ U)
+        return H @ (Pc - 0.5 * m * Qn)
+
+    reduced.folded = folded
     return reduced, direct, H
 
 
@@ -143,5 +158,47 @@ def test_chord_iteration_reaches_the_oracle_force(case):
         if np.abs(d).max() < 1e-16:
             break
     # the chord step removes the linear part exactly, so few steps are needed
+    assert it < 12
+    assert np.abs(Phi / g['J'] - ref['F'][:D]).max() <= 1e-13 * max(1e-3, np.abs(ref['F']).max())
+
+
+@pytest.mark.parametrize("case", range(7))
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.3])
+def test_folded_chord_step_equals_chord_step_of_direct_map(case, tau):
+    q, mesh, qi = _cases()[case]
+    D = 2 if q == 9 else 3
+    rng = np.random.default_rng(300 + case)
+    G = 1e-4 * rng.uniform(-1, 1, 3)
+    prm = W.params(tau, body_force=tuple(G))
+    g = cell_geometry(mesh, qi, prm)
+    U0 = 0.05 * rng.uniform(-1, 1, D)
+    N = g['J'] * equilibrium(q, 1.0, U0, U0, g['ginv'])[:q] * (1 + 0.05 * rng.uniform(-1, 1, q))
+    reduced, direct, H = _maps(q, g, tau, N, g['G'][:D])
+    for _ in range(4):
+        Phi = 0.05 * rng.uniform(-1, 1, D)
+        chord = Phi + H @ (direct(Phi) - Phi)
+        a = reduced.folded(Phi)
+        assert np.abs(a - chord).max() <= 1e-14 * max(1.0, np.abs(chord).max()), (a, chord)
+
+
+@pytest.mark.parametrize("case", range(7))
+def test_folded_chord_iteration_reaches_the_oracle_force(case):
+    q, mesh, qi = _cases()[case]
+    D = 2 if q == 9 else 3
+    tau = 0.8
+    rng = np.random.default_rng(17 + case)
+    prm = W.params(tau, body_force=(1e-5, 0, 0), tol=1e-15, max_iter=500)
+    g = cell_geometry(mesh, qi, prm)
+    U0 = 0.03 * rng.uniform(-1, 1, D)
+    N = g['J'] * equilibrium(q, 1.0, U0, U0, g['ginv'])[:q] * (1 + 0.02 * rng.uniform(-1, 1, q))
+    ref = collide(q, g, prm, N)
+    reduced, _, _ = _maps(q, g, tau, N, g['G'][:D])
+    Phi = np.zeros(D)
+    for it in range(30):
+        nxt = reduced.folded(Phi)
+        d = nxt - Phi
+        Phi = nxt
+        if np.abs(d).max() < 1e-16:
+            break
     assert it < 12
     assert np.abs(Phi / g['J'] - ref['F'][:D]).max() <= 1e-13 * max(1e-3, np.abs(ref['F']).max())
