@@ -312,22 +312,29 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
                                      arg_r<R>(a.tol, a.tol_f), a.max_iter, Np, cst);
       if (!cst.conv) atomicOr(a.err, ERR_NOCONV);
 
-      // ---- moving walls: a reflected population is corrected by
-      //      -J rho [f^eq_a - f^eq_abar](rho = 1, U = U~ = U_wall)
-      const bool moving = a.moving && ad.wall_cell();
-      R uw[D];
+      // ---- moving walls (wall cells only, one branch per cell): a reflected
+      //      population is corrected by -J rho [f^eq_a - f^eq_abar](rho = 1,
+      //      U = U~ = U_wall)
+      if (a.moving && ad.wall_cell()) {
+        R uw[D], zero[D], gd[L::NS];
 #pragma unroll
-      for (int i = 0; i < D; i++) uw[i] = moving ? rc[L::UW + i] : R(0);
-      EqParts<Q, R> ew;
-      if (moving) {
-        R zero[D], gd[L::NS];
-#pragma unroll
-        for (int i = 0; i < D; i++) zero[i] = R(0);
+        for (int i = 0; i < D; i++) {
+          uw[i] = rc[L::UW + i];
+          zero[i] = R(0);
+        }
 #pragma unroll
         for (int i = 0; i < L::NS; i++) gd[i] = rc[L::GINV + i];
+        EqParts<Q, R> ew;
         eq_parts<Q, R>(gd, uw, zero, ew);
+        const R Jr2 = R(2) * rc[L::J] * cst.rho;
+#pragma unroll
+        for (int av = 1; av < Q; av++) {
+          const int p = av <= H ? av : av - H;
+          const R corr = Jr2 * lat_w<Q, R>(av) * eq_odd<Q, R>(ew, uw, p);
+          const R nv = Np[av] - ((av <= H) ? corr : -corr);
+          Np[av] = ad.crosses(av, 1) ? nv : Np[av];
+        }
       }
-      const R Jc = moving ? rc[L::J] : R(0);
 
       // ---- push (write side of Eq. 22)
 #pragma unroll
@@ -335,17 +342,10 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
         const int ab = lat_opp<Q>(av);
         const bool crs = ad.crosses(av, 1);
         R v = Np[av];
-        if (moving && crs) {
-          const int p = av <= H ? av : av - H;
-          const R O = eq_odd<Q, R>(ew, uw, p);
-          const R corr = R(2) * Jc * cst.rho * lat_w<Q, R>(av) * O;
-          v -= (av <= H) ? corr : -corr;
-        }
         if constexpr (REFOFS) v -= rc[((!ODD || crs) ? L::ROWN : L::ROUT) + av];
-        if (!ODD || crs)
-          f[(IT)ab * ps + cell] = store_s<S>(v);
-        else
-          f[(IT)av * ps + ad.nb(av, 1)] = store_s<S>(v);
+        // one store through a selected index (own slot abar, or slot a of q + c_a)
+        const IT idx = (!ODD || crs) ? (IT)ab * ps + cell : (IT)av * ps + ad.nb(av, 1);
+        f[idx] = store_s<S>(v);
       }
       f[cell] = store_s<S>(REFOFS ? Np[0] - rc[L::ROWN] : Np[0]);
     }
