@@ -5,12 +5,17 @@ assignment of tiles to blocks differs, so a batch must reproduce the
 members' individual time steps bit for bit: uneven D3Q19 channels in plane
 mode (ragged fastest axis included), D2Q9 meshes in full mode in FP64,
 whole 32-step graph replays plus remainders, a start at odd parity, and the
-run-length tuner. Members that cannot share a launch are rejected.
+run-length tuner. Members that cannot share a launch are rejected. Each
+member of an uneven D2Q9 batch is also held to the FP64 oracle itself: at
+1e-12 in FP64 and at 2e-5 (rho, and u normalised by max|u|) in FP32.
 """
 import numpy as np
 import pytest
 
+from oracle import OracleSim
 from paper_2401_17183_gb300 import workloads as W
+
+from .helpers import rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -91,3 +96,35 @@ def test_batch_rejects_mixed_members(V):
     with pytest.raises(V.VlbError) as e:
         V.Batch(h)
     assert e.value.code == "EINVAL"
+
+
+def _uneven_d2q9():
+    """Uneven D2Q9 members: stretched 2D channels (walls, plane mode) of
+    different sizes, one with a ragged fastest axis, driven by a body force."""
+    meshes = [W.channel2d_mesh(12, 40, stretch=0.5), W.channel2d_mesh(20, 136, stretch=0.7),
+              W.channel2d_mesh(8, 24, stretch=0.3), W.channel2d_mesh(16, 256, stretch=0.6)]
+    out = []
+    for i, mesh in enumerate(meshes):
+        rho, u = W.noise_fields(mesh, amp=0.01, seed=40 + i)
+        out.append((mesh, W.params(0.8, body_force=(0.0, 1e-5, 0.0)), rho, u))
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [("F64", 1e-12), ("F32", 2e-5)])
+def test_batch_members_match_the_oracle(V, prec, tol):
+    members = _uneven_d2q9()
+    steps = 70                      # two 32-step graph replays and a remainder
+    sims = [V.Sim(V.Mesh(m), prm, rho, u, precision=getattr(V, "VLB_" + prec))
+            for (m, prm, rho, u) in members]
+    b = V.Batch(sims)
+    b.step(steps)
+    for (mesh, prm, rho, u), s in zip(members, sims):
+        s.sync()
+        o = OracleSim(mesh, prm)
+        o.init(rho, u)
+        o.step(steps)
+        om, gm = o.moments(), s.moments()
+        su = np.abs(om["u"]).max()
+        assert rel_err(gm["rho"], om["rho"], 1.0) < tol
+        assert rel_err(gm["u"], om["u"], su) < tol
+        assert rel_err(gm["u_tilde"], om["u_tilde"], su) < tol

@@ -100,9 +100,11 @@ def test_training_reduces_loss(NN):
     target = torch.tanh(dx[:, :3] + 0.5 * dx[:, 1:4]).contiguous()
     B = x.shape[0]
     losses = []
-    for it in range(1, 151):
+    # measured loss ratio after 150 / 300 iterations: 0.148 / 0.073 (bfloat16
+    # storage), 0.159 / 0.080 (FP32 storage): 300 iterations reach a tenth
+    for it in range(1, 301):
         net.forward(dx.data_ptr(), dy.data_ptr(), B)
         losses.append(net.mse(dy.data_ptr(), target.data_ptr(), ddy.data_ptr(), B))
         net.backward(ddy.data_ptr(), B)
         net.adam(3e-3, it)
-    assert losses[-1] < 0.25 * losses[0], (losses[0], losses[-1])
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])

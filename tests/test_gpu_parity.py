@@ -237,6 +237,35 @@ def test_channel_fp32(V, channel_oracle):
         _cmp_moments(g.moments(), m200, 2e-5)
 
 
+@pytest.fixture(scope="module")
+def channel_tiles_oracle():
+    """D3Q19 channel whose periodic fastest axis is one whole 128-cell tile
+    (4 x 5 x 128, plane mode): tanh wall-normal stretching 0.7 (J, g^ij and
+    Theta vary across the channel), walls, body force along xi, tau = 0.6, 1%
+    seeded velocity noise; 1000 oracle steps (about half a minute)."""
+    mesh = W.channel_mesh(4, 5, 128, stretch=0.7, bump=0.0)
+    prm = W.params(0.6, body_force=(2e-5, 0, 0))
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=11)
+    o = OracleSim(mesh, prm)
+    o.init(rho, u)
+    o.step(1000)
+    return mesh, prm, rho, u, o.moments()
+
+
+def test_channel_fp32_1000_steps_whole_tiles(V, channel_tiles_oracle):
+    """The FP32 D3Q19 kernel of the benchmark against the FP64 oracle after
+    1000 steps (<= 2e-5 on rho and on u, u normalised by max|u|): even steps
+    take the 16-byte row copies of whole tiles, odd steps the neighbour
+    gathers, both with walls and a body force."""
+    mesh, prm, rho, u, om = channel_tiles_oracle
+    g = V.Sim(V.Mesh(mesh), prm, rho, u, precision=V.VLB_F32)
+    assert g.layout()["plane"]
+    g.step(1000)
+    gm = g.moments()
+    _cmp_moments(gm, om, 2e-5)
+    assert abs(gm["mass"] - om["mass"]) <= 2e-5 * om["mass"]
+
+
 def test_couette_on_gpu_matches_closed_form(V):
     """The GPU path on the narrow-gap wedge (128 radial cells) from rest, and a
     full annulus (FP32) started from the closed form."""

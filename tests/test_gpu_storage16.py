@@ -47,7 +47,10 @@ def channel(request):
 
 
 # (precision name, reference, max rel. error of u (to max|u|), of rho, of the mass drift over
-# 200 steps)
+# 200 steps). Rounding a population to 16 bits does not conserve mass; the
+# drift of the total over the run, measured from the run's own (rounded)
+# start, was at most 4.1e-6 (FP16) and 4.4e-5 (bfloat16) over the four cases
+# and both row parities, so the bounds leave a factor of about five.
 CASES = [("F16", "REST", 1e-3, 5e-4, 2e-5), ("F16", "UNIFORM", 2e-3, 1e-3, 2e-5),
          ("BF16", "REST", 1e-2, 5e-3, 2e-4), ("BF16", "UNIFORM", 1e-2, 5e-3, 2e-4)]
 
@@ -107,7 +110,9 @@ def test_channel2d_d2q9_16bit(V):
         s = V.Sim(gm, prm, rho, u, precision=getattr(V, "VLB_" + prec), reference=V.VLB_REF_REST)
         assert s.layout()["plane"]
         s.step(500)
-        assert rel_err(s.moments()["u"], mr["u"], su) < tol, prec
+        sm = s.moments()
+        assert rel_err(sm["u"], mr["u"], su) < tol, prec
+        assert rel_err(sm["u_tilde"], mr["u_tilde"], su) < tol, prec
 
 
 @pytest.mark.parametrize("prec", ["F16", "BF16"])
