@@ -521,14 +521,29 @@ def main():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         sim.reset_ptr(pin_rho.data_ptr(), pin_u.data_ptr())
+        t1 = time.perf_counter()
         sim.step(a.steps)
+        t2 = time.perf_counter()
         sim.moments_ptr(out_rho.data_ptr(), out_u.data_ptr(), out_ut.data_ptr(), out_t.data_ptr())
-        el = max_over_ranks(time.perf_counter() - t0, dev)
+        t3 = time.perf_counter()
+        el = max_over_ranks(t3 - t0, dev)
+        # after the timed region: the moments kernels alone (totals only to the
+        # host), so that the device-to-host copy of the fields can be told apart
+        sim.moments_ptr(0, 0, 0, out_t.data_ptr())
+        t4 = time.perf_counter()
+        sim.moments_ptr(0, 0, 0, out_t.data_ptr())
+        t5 = time.perf_counter()
         h2d = 8 * ncell * 4
         d2h = 8 * ncell * 7 + 56
         e2e = {"value": job_mlups(world, ncell, a.steps, el), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
-               "api": "vlb_reset(host rho,u) + vlb_step(K) + vlb_moments(host rho,u,u~,totals)"}
+               "api": "vlb_reset(host rho,u) + vlb_step(K) + vlb_moments(host rho,u,u~,totals)",
+               # reset: H2D of rho and u plus the initialisation kernel; steps: the
+               # device-timed K steps; moments: the moments and totals kernels with
+               # only the totals copied back; d2h: the rest of the time from the
+               # step launches to the end of vlb_moments (the fields' copy)
+               "phases_s": {"reset": t1 - t0, "steps": ms / 1e3, "moments_kernels": t5 - t4,
+                            "fields_d2h": max(0.0, (t3 - t1) - ms / 1e3 - (t5 - t4))}}
 
     if rank != 0:
         if world > 1:

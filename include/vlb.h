@@ -250,8 +250,10 @@ void vlb_batch_destroy(vlb_batch *b);
  * Its per-block partial sums live in a fixed device array of 4096 x 7 doubles
  * (224 KiB) that every device which loads the library holds until the process
  * exits; meshes of more than 4096 x 16384 = 67,108,864 cells are rejected
- * with VLB_EINVAL. The first call on a device looks up that array's device
- * address; make the first call before any stream capture. All calls share the
+ * with VLB_EINVAL. The kernels are those of vlb_moments' totals; they run on
+ * the mesh's device (the call makes it current for the launches and restores
+ * the caller's device). The first call on a device looks up that array's
+ * device address; make the first call before any stream capture. All calls share the
  * array, so calls that overlap on the GPU (for example on two streams) race
  * and give wrong totals; every call writes each slot it reads before reading
  * it, so nothing needs clearing. D2Q9 and D3Q19 simulations only (D3Q39:

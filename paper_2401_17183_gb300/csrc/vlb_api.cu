@@ -399,9 +399,13 @@ int vlb_moments(vlb_sim *s, double *rho, double *u, double *u_tilde, double *tot
     CU(cudaMalloc(&s->d_partial, sizeof(double) * 7 * 4 * 152));
     CU(cudaMalloc(&s->d_totals, sizeof(double) * 7));
   }
-  CU(m->md.q == VLB_D3Q39 ? vlb::q39_moments(s, s->d_fields, s->d_partial, nblk, s->stream)
-                          : vlb::launch_moments(s, s->d_fields, s->d_partial, nblk, s->stream));
-  CU(vlb::launch_finish_totals(s->d_partial, nblk, s->d_totals, s->stream));
+  if (m->md.q == VLB_D3Q39) {
+    CU(vlb::q39_moments(s, s->d_fields, s->d_partial, nblk, s->stream));
+    CU(vlb::launch_finish_totals(s->d_partial, nblk, s->d_totals, s->stream));
+  } else {
+    CU(vlb::launch_moments(s, s->d_fields, nblk, s->stream));
+    CU(vlb::launch_totals(s, s->d_partial, 4 * 152, s->d_totals, s->stream));
+  }
   int rc = check_kernel_flags(s->d_err, s->stream);
   if (rc) return rc;
   if (totals) {

@@ -478,8 +478,11 @@ cudaError_t launch_plane_check(const vlb_mesh *m, int *d_flag, cudaStream_t s);
 cudaError_t launch_pack_coef(const vlb_sim *sim, cudaStream_t s);
 cudaError_t launch_init(const vlb_sim *sim, const double *d_rho, const double *d_u, cudaStream_t s);
 cudaError_t launch_step(const vlb_sim *sim, int odd, cudaStream_t s);
-cudaError_t launch_moments(const vlb_sim *sim, double *d_out, double *d_partial, int64_t nblk,
-                           cudaStream_t s);
+cudaError_t launch_moments(const vlb_sim *sim, double *d_out, int64_t nblk, cudaStream_t s);
+// conservation totals (mass, P, M) of a D2Q9/D3Q19 simulation into d_totals[7]
+// through per-block partial sums in d_partial (room for nblk_max x 7 doubles)
+cudaError_t launch_totals(const vlb_sim *sim, double *d_partial, int64_t nblk_max, double *d_totals,
+                          cudaStream_t s);
 cudaError_t launch_finish_totals(const double *d_partial, int64_t nblk, double *d_totals,
                                  cudaStream_t s);
 cudaError_t launch_get_state(const vlb_sim *sim, double *d_N, cudaStream_t s);

@@ -69,3 +69,27 @@ def test_totals_noalloc_rejects_null_output():
     with pytest.raises(V.VlbError) as e:
         sim.totals_noalloc(0)
     assert e.value.code == "EINVAL"
+
+
+def test_totals_noalloc_runs_on_the_mesh_device():
+    """Called with another device current, the call still runs on the mesh's
+    device (whose scratch address it uses) and leaves the caller's device
+    current. Needs two GPUs."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    V = _lib()
+    torch.cuda.set_device(0)
+    mesh = W.channel_mesh(16, 12, 8, stretch=0.7, bump=0.05)
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+    sim = V.Sim(V.Mesh(mesh), W.params(0.8), rho, u, precision=V.VLB_F64)
+    sim.step(2)
+    out = torch.full((7,), float("nan"), dtype=torch.float64, device="cuda:0")
+    torch.cuda.set_device(1)
+    sim.totals_noalloc(out.data_ptr())
+    assert torch.cuda.current_device() == 1
+    torch.cuda.set_device(0)
+    sim.sync()
+    torch.cuda.synchronize(0)
+    exp = _expected(sim.moments(fields=False), 3)
+    assert np.abs(out.cpu().numpy() - exp).max() <= 1e-12 * exp[0]
