@@ -40,6 +40,9 @@ sys.path.insert(0, ROOT)
 BYTES_PER_CELL = {("19", "f32"): 2 * 19 * 4, ("19", "f64"): 2 * 19 * 8, ("9", "f32"): 2 * 9 * 4,
                   ("9", "f64"): 2 * 9 * 8, ("19", "f16"): 2 * 19 * 2, ("19", "bf16"): 2 * 19 * 2}
 STEP_SOURCES = ["vlb_step.cu", "vlb_step.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_internal.cuh"]
+# the coefficient record values the D3Q19 FP32 step kernel reads per cell
+# (CoefLayout<19>::ROWN: everything before the 16-bit storage offsets)
+RECORD_FLOATS_READ = 172
 
 
 def args_parse():
@@ -53,6 +56,11 @@ def args_parse():
     ap.add_argument("--bump", type=float, default=0.05)
     ap.add_argument("--tau", type=float, default=0.8)
     ap.add_argument("--coef-mode", default="auto", choices=["auto", "full", "plane"])
+    ap.add_argument("--mesh", default="channel", choices=["channel", "bump3d"],
+                    help="bump3d: the lower-wall bump also varies spanwise (per-cell coefficient records)")
+    ap.add_argument("--general-n", type=int, default=256,
+                    help="cells per axis of the general-mesh leg (0 skips it)")
+    ap.add_argument("--general-steps", type=int, default=200)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage (arithmetic stays FP32)")
     ap.add_argument("--reference", default="rest", choices=["uniform", "rest"],
@@ -87,10 +95,10 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(ncell):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current step-kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "step_d3q19_f32_channel_ncu.md")
+def ncu_traffic(ncell, name="step_d3q19_f32_channel_ncu.md"):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current step-kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(p).read()
     except OSError:
@@ -233,6 +241,57 @@ def cpu_baseline_leg(tau, stretch, bump):
             "sample": "32x32x16 cells of the same channel family (D3Q19, FP64, stretch %g, "
                       "bump %g h, tau %g), %d steps, %.1f s, single thread"
                       % (stretch, bump, tau, k, el)}
+
+
+def general_mesh_leg(a, stream):
+    """The same fused step on a mesh whose geometry varies along every axis (a
+    channel whose lower-wall bump also varies spanwise): one coefficient record
+    per cell, streamed from HBM with the populations. FP32, --general-n^3 cells,
+    --general-steps timed steps after 5 warm-up steps."""
+    import torch
+
+    from paper_2401_17183_gb300 import vlb
+    from paper_2401_17183_gb300 import workloads as W
+    n = a.general_n
+    mesh = W.channel_bump3d_mesh(n, n, n, stretch=a.stretch, bump=a.bump)
+    prm = W.params(a.tau, body_force=(1e-6, 0.0, 0.0))
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+    ncell = W.ncell(mesh)
+    gm = vlb.Mesh(mesh)
+    del mesh
+    sim = vlb.Sim(gm, prm, rho, u, precision=vlb.VLB_F32, coef_mode=vlb.VLB_COEF_FULL,
+                  stream=stream.cuda_stream)
+    lay = sim.layout()
+    sim.step(5)
+    sim.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(a.general_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.sync()
+    value = ncell * a.general_steps / (ms / 1e3) / 1e6
+    peak, peak_kind = measured_peak_hbm()
+    # bytes the kernel moves per cell update: populations read and written, and
+    # the part of the cell's coefficient record it reads
+    rec_bytes = 4 * RECORD_FLOATS_READ
+    per_launch = ms / 1e3 / a.general_steps
+    out = {"workload": "channel_bump3d_d3q19_%d^3_fp32_full_records" % n, "cells": ncell,
+           "value": value, "unit": "MLUPS", "steps": a.general_steps,
+           "ms_per_step": ms / a.general_steps, "coef_mode": "plane" if lay["plane"] else "full",
+           "record_floats_stored": lay["coef_per_cell"], "record_bytes_read_per_cell": rec_bytes,
+           "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+                        "achieved_populations": 152 * ncell / per_launch / 1e9,
+                        "frac_populations": 152 * ncell / per_launch / 1e9 / peak,
+                        "achieved_with_records": (152 + rec_bytes) * ncell / per_launch / 1e9,
+                        "frac_with_records": (152 + rec_bytes) * ncell / per_launch / 1e9 / peak,
+                        "traffic": ncu_traffic(ncell, "step_d3q19_f32_bump3d_full_ncu.md")}}
+    sim.close()
+    gm.close()
+    return out
 
 
 def batch_meshes(nmesh, seed=4):
@@ -462,7 +521,10 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    mesh = W.channel_mesh(a.n, a.n, a.n, stretch=a.stretch, bump=a.bump)
+    make = W.channel_bump3d_mesh if a.mesh == "bump3d" else W.channel_mesh
+    mesh = make(a.n, a.n, a.n, stretch=a.stretch, bump=a.bump)
+    if a.mesh == "bump3d":
+        cfg["workload"] = cfg["workload"].replace("channel_", "channel_bump3d_")
     prm = W.params(a.tau, body_force=(1e-6, 0.0, 0.0))
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
     ncell = W.ncell(mesh)
@@ -545,6 +607,10 @@ def main():
                "phases_s": {"reset": t1 - t0, "steps": ms / 1e3, "moments_kernels": t5 - t4,
                             "fields_d2h": max(0.0, (t3 - t1) - ms / 1e3 - (t5 - t4))}}
 
+    general = None
+    if a.general_n > 0 and a.mesh == "channel" and a.storage == "f32" and world == 1:
+        del sim, gmesh
+        general = general_mesh_leg(a, stream)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -564,6 +630,7 @@ def main():
                                                         "bf16": "__nv_bfloat16"}[a.storage],
                      "source_sha": source_sha()},
         "clocks": clocks, "e2e": e2e, "gpu_launches": a.steps, "cpu_baseline": cpu,
+        "general_mesh": general,
     }
     print(json.dumps(line))
     if world > 1:

@@ -198,7 +198,7 @@ struct TotArgs {
 // velocity components by a runtime direction index (constant memory)
 template <int Q>
 struct DirTable {
-  int8_t c[Q][3];
+  int8_t c[Q][4];
 };
 template <int Q>
 constexpr DirTable<Q> make_dir_table() {
@@ -213,6 +213,7 @@ template <int Q>
 __device__ __forceinline__ const int8_t *dir_table(int a) {
   return Q == 9 ? kDir9.c[a] : kDir19.c[a];
 }
+
 // does q - c_a leave the domain through a wall (runtime direction)
 template <int Q, typename IT>
 __device__ __forceinline__ bool crosses_rt(const Addr<Q, IT> &ad, const int8_t *cv) {

@@ -137,6 +137,25 @@ def channel_mesh(n0=256, n1=256, n2=256, stretch=2.5, bump=0.05, wall_links=0):
                  shift=[[n0, 0, 0], [0, 0, 0], [0, 0, n2]], wall_links=wall_links)
 
 
+def channel_bump3d_mesh(n0=256, n1=256, n2=256, stretch=0.7, bump=0.05, wall_links=0):
+    """3D channel as channel_mesh, but the lower-wall bump also varies along
+    the spanwise axis, bump h sin(2 pi x / (n0/2)) cos(2 pi z / (n2/2)), so the
+    geometry changes along every axis (no plane-invariant records)."""
+    h = 0.5 * n1
+    xi = np.arange(n0, dtype=np.float64)
+    eta = np.arange(n1, dtype=np.float64)
+    zeta = np.arange(n2, dtype=np.float64)
+    s = 2.0 * (eta + 0.5) / n1 - 1.0
+    ys = h * np.tanh(stretch * s) / math.tanh(stretch) if stretch > 0 else h * s
+    bl = (bump * h * np.sin(2 * np.pi * xi / (0.5 * n0)))[:, None] * np.cos(2 * np.pi * zeta / (0.5 * n2))[None, :]
+    X = np.empty((n0, n1, n2, 3))
+    X[..., 0] = xi[:, None, None]
+    X[..., 1] = ys[None, :, None] + bl[:, None, :] * (1.0 - ys[None, :, None] / h) / 2.0
+    X[..., 2] = zeta[None, None, :]
+    return _mesh(3, (n0, n1, n2), X, (PERIODIC, WALL, PERIODIC),
+                 shift=[[n0, 0, 0], [0, 0, 0], [0, 0, n2]], wall_links=wall_links)
+
+
 def channel2d_mesh(n0=32, n1=16, stretch=0.7, wall_links=0, bump=0.0):
     """2D channel: axis 0 wall-normal with walls and tanh stretching (as in
     channel_mesh), axis 1 streamwise, periodic and fastest in memory. Without
