@@ -61,6 +61,11 @@ def args_parse():
     ap.add_argument("--general-n", type=int, default=256,
                     help="cells per axis of the general-mesh leg (0 skips it)")
     ap.add_argument("--general-steps", type=int, default=200)
+    ap.add_argument("--no-time-to-steady", action="store_true",
+                    help="skip the reduced warm-start comparison of the default run")
+    ap.add_argument("--tts-train", type=int, default=512)
+    ap.add_argument("--tts-test", type=int, default=64)
+    ap.add_argument("--tts-iters", type=int, default=1000)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage (arithmetic stays FP32)")
     ap.add_argument("--reference", default="rest", choices=["uniform", "rest"],
@@ -176,71 +181,118 @@ def job_mlups(world, ncell, steps, seconds):
 
 
 def cpu_model():
+    """Host CPU model and logical CPU count, from lscpu (else /proc/cpuinfo)."""
+    info = {"model": None, "cpus": os.cpu_count(), "source": "os"}
     try:
-        for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
-                return line.split(":", 1)[1].strip()
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k == "Model name" and info["model"] is None:
+                info["model"] = v
+            elif k == "CPU(s)":
+                info["cpus"] = int(v)
+            elif k == "Vendor ID":
+                info["vendor"] = v
+        info["source"] = "lscpu"
+    except Exception:
         pass
-    return os.uname().machine
+    if info["model"] is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    info["model"] = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            info["model"] = os.uname().machine
+    return info
 
 
-def reference_sample_run(steps, warmup, tau, stretch, bump, budget_s=120.0):
-    """The FP64 oracle on the host cores, on a bounded sample of the channel family."""
+def _oracle_replica(job):
+    """One oracle run on its own sample (a spawned process): returns the
+    seconds of the timed steps."""
+    n, steps, warmup, tau, stretch, bump = job
+    sys.path.insert(0, ROOT)
     from oracle import OracleSim
     from paper_2401_17183_gb300 import workloads as W
-    prm = W.params(tau, body_force=(1e-6, 0.0, 0.0))
-
-    def run(s, k):
-        mesh = W.channel_mesh(s, s, s, stretch=stretch, bump=bump)
-        rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
-        o = OracleSim(mesh, prm)
-        o.init(rho, u)
-        t = time.perf_counter()
-        o.step(k)
-        return time.perf_counter() - t, s ** 3
-
-    dt, nc = run(6, 1)
-    per_cell = dt / nc
-    per_step_budget = budget_s / max(1, steps + warmup)
-    s = 4
-    while (s + 2) ** 3 * per_cell <= per_step_budget and s < 32:
-        s += 2
-    mesh = W.channel_mesh(s, s, s, stretch=stretch, bump=bump)
+    mesh = W.channel_mesh(*n, stretch=stretch, bump=bump)
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
-    o = OracleSim(mesh, prm)
+    o = OracleSim(mesh, W.params(tau, body_force=(1e-6, 0.0, 0.0)))
     o.init(rho, u)
     o.step(warmup)
     t = time.perf_counter()
     o.step(steps)
-    el = time.perf_counter() - t
-    return {"value": s ** 3 * steps / el / 1e6, "cells": s ** 3, "steps": steps, "seconds": el,
-            "sample": "%d^3 cells of the same channel family (stretch %g, bump %g h, walls, "
-                      "body force, tau %g), %d timed steps" % (s, stretch, bump, tau, steps)}
+    return time.perf_counter() - t
 
 
-def cpu_baseline_leg(tau, stretch, bump):
-    """Oracle MLUPS on a bounded sample (about 10-20 s of CPU work), 1 thread."""
+def oracle_on_cores(n, steps, warmup, tau, stretch, bump, procs):
+    """The oracle as it stands on `procs` host cores at once: independent
+    replicas of the same sample in spawned processes (no shared state, no
+    change to the oracle). Returns (aggregate MLUPS, slowest replica's seconds)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    job = (n, steps, warmup, tau, stretch, bump)
+    with ctx.Pool(procs) as pool:
+        secs = pool.map(_oracle_replica, [job] * procs)
+    cells = n[0] * n[1] * n[2]
+    return procs * cells * steps / max(secs) / 1e6, max(secs)
+
+
+def reference_sample_run(steps, warmup, tau, stretch, bump, budget_s=120.0):
+    """The FP64 oracle on all host cores (one replica per core), on a bounded
+    sample of the channel family sized so that the run fits budget_s."""
     from oracle import OracleSim
     from paper_2401_17183_gb300 import workloads as W
     prm = W.params(tau, body_force=(1e-6, 0.0, 0.0))
-    mesh = W.channel_mesh(32, 32, 16, stretch=stretch, bump=bump)
+    mesh = W.channel_mesh(6, 6, 6, stretch=stretch, bump=bump)
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+    o = OracleSim(mesh, prm)
+    o.init(rho, u)
+    t = time.perf_counter()
+    o.step(1)
+    per_cell = (time.perf_counter() - t) / 216
+    per_step_budget = budget_s / max(1, steps + warmup)
+    s = 4
+    while (s + 2) ** 3 * per_cell <= per_step_budget and s < 32:
+        s += 2
+    cpu = cpu_model()
+    procs = max(1, int(cpu["cpus"] or 1))
+    value, el = oracle_on_cores((s, s, s), steps, warmup, tau, stretch, bump, procs)
+    return {"value": value, "cells": s ** 3, "steps": steps, "seconds": el, "cores": procs, "cpu": cpu,
+            "sample": "%d^3 cells of the same channel family (stretch %g, bump %g h, walls, body force, "
+                      "tau %g), %d timed steps, one independent replica per core on %d cores"
+                      % (s, stretch, bump, tau, steps, procs)}
+
+
+def cpu_baseline_leg(tau, stretch, bump):
+    """Oracle MLUPS on a bounded sample (32 x 32 x 16 cells of the channel
+    family): single-threaded, and on every host core at once (one replica per
+    core, spawned processes); about 10-20 s of CPU work each."""
+    from oracle import OracleSim
+    from paper_2401_17183_gb300 import workloads as W
+    prm = W.params(tau, body_force=(1e-6, 0.0, 0.0))
+    n = (32, 32, 16)
+    mesh = W.channel_mesh(*n, stretch=stretch, bump=bump)
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
     o = OracleSim(mesh, prm)
     o.init(rho, u)
     o.step(1)
     t = time.perf_counter()
     k = 0
-    while k < 3 or (time.perf_counter() - t < 12.0 and k < 200):
+    while k < 3 or (time.perf_counter() - t < 10.0 and k < 200):
         o.step(1)
         k += 1
     el = time.perf_counter() - t
-    nc = 32 * 32 * 16
-    return {"value": nc * k / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "cpu": cpu_model(),
-            "sample": "32x32x16 cells of the same channel family (D3Q19, FP64, stretch %g, "
-                      "bump %g h, tau %g), %d steps, %.1f s, single thread"
-                      % (stretch, bump, tau, k, el)}
+    nc = n[0] * n[1] * n[2]
+    single = nc * k / el / 1e6
+    cpu = cpu_model()
+    procs = max(1, int(cpu["cpus"] or 1))
+    allc, el_all = oracle_on_cores(n, k, 1, tau, stretch, bump, procs)
+    return {"value": allc, "unit": "MLUPS", "cores": procs, "kind": "oracle", "cpu": cpu,
+            "sample": "32x32x16 cells of the same channel family (D3Q19, FP64, stretch %g, bump %g h, "
+                      "tau %g), %d steps; one independent replica per core on %d cores (%.1f s)"
+                      % (stretch, bump, tau, k, procs, el_all),
+            "single_thread": {"value": single, "unit": "MLUPS", "cores": 1, "seconds": el}}
 
 
 def general_mesh_leg(a, stream):
@@ -424,20 +476,18 @@ def bench_d3q39(a):
     print(json.dumps(line))
 
 
-def bench_warmstart(a):
+def warmstart_leg(ntrain, ntest, iters):
     """Steps and wall time to a 1e-6 residual from the learned prediction and
     from rest, on held-out members of the bumped 2D channel family."""
     import numpy as np
 
-    from paper_2401_17183_gb300 import build as B
-    B.build()
     from paper_2401_17183_gb300 import warmstart as WS
     t0 = time.perf_counter()
-    X, Y, keep = WS.dataset(WS.family(4, a.ntrain))
+    X, Y, keep = WS.dataset(WS.family(4, ntrain))
     t_data = time.perf_counter() - t0
     ws = WS.WarmStart()
-    losses, t_train = ws.train(X, Y, a.iters)
-    test = WS.family(5, a.ntest)
+    losses, t_train = ws.train(X, Y, iters)
+    test = WS.family(5, ntest)
     Xt, Yt, kt = WS.dataset(test)
     tspec = [test[k] for k in kt]
     t1 = time.perf_counter()
@@ -449,21 +499,33 @@ def bench_warmstart(a):
     sc, tc = WS.run_to_steady(cold)
     warm = [m[2] for m in WS.make_sims(tspec, init=pred)]
     sw, tw = WS.run_to_steady(warm)
-    line = {
-        "metric": "time-to-steady (1e-6 residual), learned warm start vs plain cold start",
+    return {
         "value": float(sc.mean() / sw.mean()), "unit": "x fewer steps (mean over held-out members)",
-        "n_gpus": 1, "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 solver; bf16 network storage with f32 accumulation",
-        "data": "synthetic (seeded bumped 2D channels; steady targets from the solver)",
         "config": {"workload": "warmstart_channel2d_32x64_d2q9", "train_members": len(keep),
-                   "test_members": len(kt), "iters": a.iters, "batch": ws.batch,
-                   "params": ws.net.nparams, "tau": WS.TAU},
+                   "test_members": len(kt), "iters": iters, "batch": ws.batch,
+                   "params": ws.net.nparams, "tau": WS.TAU, "residual": 1e-6},
         "cold": {"steps_mean": float(sc.mean()), "steps_max": int(sc.max()), "wall_s": tc},
         "warm": {"steps_mean": float(sw.mean()), "steps_max": int(sw.max()), "wall_s": tw + t_pred,
                  "inference_s": t_pred},
+        "wall_speedup": float(tc / (tw + t_pred)),
         "prediction_u_rel_err": {"mean": float(np.mean(err)), "max": float(np.max(err))},
         "train": {"loss_first": losses[0], "loss_last": losses[-1], "seconds": t_train,
                   "data_seconds": t_data},
+    }
+
+
+def bench_warmstart(a):
+    from paper_2401_17183_gb300 import build as B
+    B.build()
+    r = warmstart_leg(a.ntrain, a.ntest, a.iters)
+    line = {
+        "metric": "time-to-steady (1e-6 residual), learned warm start vs plain cold start",
+        "value": r["value"], "unit": r["unit"],
+        "n_gpus": 1, "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 solver; bf16 network storage with f32 accumulation",
+        "data": "synthetic (seeded bumped 2D channels; steady targets from the solver)",
+        "config": r["config"], "cold": r["cold"], "warm": r["warm"], "wall_speedup": r["wall_speedup"],
+        "prediction_u_rel_err": r["prediction_u_rel_err"], "train": r["train"],
     }
     print(json.dumps(line))
 
@@ -498,8 +560,8 @@ def main():
                 "ms_per_step": 1e3 * r["seconds"] / r["steps"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": cfg,
-                "cpu_baseline": {"value": r["value"], "unit": "MLUPS", "cores": 1,
-                                 "kind": "oracle", "sample": r["sample"], "cpu": cpu_model()},
+                "cpu_baseline": {"value": r["value"], "unit": "MLUPS", "cores": r["cores"],
+                                 "kind": "oracle", "sample": r["sample"], "cpu": r["cpu"]},
                 "e2e": {"value": r["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -607,10 +669,14 @@ def main():
                "phases_s": {"reset": t1 - t0, "steps": ms / 1e3, "moments_kernels": t5 - t4,
                             "fields_d2h": max(0.0, (t3 - t1) - ms / 1e3 - (t5 - t4))}}
 
-    general = None
+    general = tts = None
     if a.general_n > 0 and a.mesh == "channel" and a.storage == "f32" and world == 1:
         del sim, gmesh
         general = general_mesh_leg(a, stream)
+    if not a.no_time_to_steady and a.mesh == "channel" and a.storage == "f32" and world == 1:
+        # the second half of the metric: time to a 1e-6 residual, learned warm
+        # start against the cold start (a reduced training set that fits the run)
+        tts = warmstart_leg(a.tts_train, a.tts_test, a.tts_iters)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -630,7 +696,7 @@ def main():
                                                         "bf16": "__nv_bfloat16"}[a.storage],
                      "source_sha": source_sha()},
         "clocks": clocks, "e2e": e2e, "gpu_launches": a.steps, "cpu_baseline": cpu,
-        "general_mesh": general,
+        "general_mesh": general, "time_to_steady": tts,
     }
     print(json.dumps(line))
     if world > 1:
