@@ -19,6 +19,9 @@ update) reaches.
                   [--workload batch --nmesh M]   (M uneven D2Q9 meshes, one launch per step)
                   [--workload warmstart --ntrain N --ntest M --iters K]   (learned warm start)
                   [--workload d3q39 --n N]   (6th-order isotropic set, FP64, N^3 periodic box)
+                  [--workload precision --n 384 --drift-steps 10000]   (FP32 / FP16 / BF16
+                      storage: MLUPS at N^3, error against the FP64 GPU path and the
+                      oracle on a 64^3 instance, total-mass drift)
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the workload,
 no collective on the data path (weak scaling); timing is the max over ranks.
@@ -41,7 +44,7 @@ BYTES_PER_CELL = {("19", "f32"): 2 * 19 * 4, ("19", "f64"): 2 * 19 * 8, ("9", "f
                   ("9", "f64"): 2 * 9 * 8, ("19", "f16"): 2 * 19 * 2, ("19", "bf16"): 2 * 19 * 2}
 STEP_SOURCES = ["vlb_step.cu", "vlb_step.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_internal.cuh"]
 # the coefficient record values the D3Q19 FP32 step kernel reads per cell
-# (CoefLayout<19>::ROWN: everything before the 16-bit storage offsets)
+# (CoefLayout<19>::SREST: everything before the 16-bit rest-relative block)
 RECORD_FLOATS_READ = 172
 
 
@@ -70,9 +73,14 @@ def args_parse():
                     help="population storage (arithmetic stays FP32)")
     ap.add_argument("--reference", default="rest", choices=["uniform", "rest"],
                     help="storage reference of 16-bit populations")
+    ap.add_argument("--no-storage16", action="store_true",
+                    help="skip the FP16-storage leg of the default run")
+    ap.add_argument("--drift-steps", type=int, default=10000,
+                    help="precision workload: steps of the total-mass drift runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="channel", choices=["channel", "batch", "warmstart", "d3q39"],
+    ap.add_argument("--workload", default="channel",
+                    choices=["channel", "batch", "warmstart", "d3q39", "precision"],
                     help="batch: many uneven D2Q9 meshes advanced by one launch per step; "
                          "warmstart: train the warm-start network and compare time to steady")
     ap.add_argument("--ntrain", type=int, default=2048)
@@ -476,6 +484,162 @@ def bench_d3q39(a):
     print(json.dumps(line))
 
 
+def time_steps(sim, steps, warmup, stream):
+    """Device time (ms) of `steps` time steps of one simulation after `warmup`
+    untimed ones: CUDA events on the launching stream, synchronised on both
+    sides."""
+    import torch
+    sim.step(warmup)
+    sim.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    return e0.elapsed_time(e1)
+
+
+def storage16_leg(a, gmesh, prm, rho, u, stream, storage="f16"):
+    """The same workload with 16-bit population storage relative to the rest
+    state (FP32 arithmetic), timed like the headline."""
+    from paper_2401_17183_gb300 import vlb
+    prec = {"f16": vlb.VLB_F16, "bf16": vlb.VLB_BF16}[storage]
+    sim = vlb.Sim(gmesh, prm, rho, u, precision=prec, stream=stream.cuda_stream,
+                  reference=vlb.VLB_REF_REST)
+    ms = time_steps(sim, a.steps, a.warmup, stream)
+    sim.close()
+    ncell = a.n ** 3
+    peak, peak_kind = measured_peak_hbm()
+    bpc = BYTES_PER_CELL[("19", storage)]
+    achieved = bpc * ncell / (ms / 1e3 / a.steps) / 1e9
+    return {"storage": storage, "reference": "rest", "value": ncell * a.steps / (ms / 1e3) / 1e6,
+            "unit": "MLUPS", "ms_per_step": ms / a.steps, "steps": a.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_cell_update": bpc,
+                         "kernel": "k_step<19,%s,float>" % ("__half" if storage == "f16" else "__nv_bfloat16")}}
+
+
+PRECISION_FORMS = [("f64", "uniform"), ("f32", "uniform"), ("f16", "rest"), ("f16", "uniform"),
+                   ("bf16", "rest"), ("bf16", "uniform")]
+
+
+def precision_accuracy(stream, drift_steps):
+    """Every storage form on the 64^3 instance of workloads.precision_instance:
+    max |rho - rho_ref| and max |u - u_ref| / max |u_ref| against the FP64 GPU
+    run and, where tests/golden/precision64_oracle.npz exists (written by
+    tests/golden/precision_reference.py, which runs only the oracle), against
+    the oracle, at its checkpoints; and the relative drift of the total mass
+    over drift_steps steps from the run's own start."""
+    import numpy as np
+
+    from paper_2401_17183_gb300 import vlb
+    from paper_2401_17183_gb300 import workloads as W
+    n = 64
+    mesh, prm, rho, u = W.precision_instance(n)
+    gm = vlb.Mesh(mesh)
+    ref_path = os.path.join(ROOT, "tests", "golden", "precision%d_oracle.npz" % n)
+    orc = dict(np.load(ref_path)) if os.path.exists(ref_path) else None
+    marks = [int(s) for s in orc["steps"]] if orc is not None else [200, 1000]
+    prec = {"f64": vlb.VLB_F64, "f32": vlb.VLB_F32, "f16": vlb.VLB_F16, "bf16": vlb.VLB_BF16}
+
+    def errs(mo, r, uu):
+        su = np.abs(uu).max()
+        return {"rho_abs": float(np.abs(mo["rho"] - r).max()), "u_rel": float(np.abs(mo["u"] - uu).max() / su)}
+
+    fields, out = {}, {}
+    for st, rf in PRECISION_FORMS:
+        name = st if st in ("f64", "f32") else "%s_%s" % (st, rf)
+        sim = vlb.Sim(gm, prm, rho, u, precision=prec[st], stream=stream.cuda_stream,
+                      reference=vlb.VLB_REF_REST if rf == "rest" else vlb.VLB_REF_UNIFORM)
+        res, done = {}, 0
+        for k in marks:
+            sim.step(k - done)
+            done = k
+            mo = sim.moments()
+            fields[(name, k)] = mo
+            r = {}
+            if name != "f64":
+                f64 = fields[("f64", k)]
+                r["vs_fp64_gpu"] = errs(mo, f64["rho"], f64["u"])
+            if orc is not None:
+                r["vs_oracle"] = errs(mo, orc["rho_%d" % k], orc["u_%d" % k])
+            res[str(k)] = r
+        sim.close()
+        # total-mass drift from the run's own (rounded) start
+        sim = vlb.Sim(gm, prm, rho, u, precision=prec[st], stream=stream.cuda_stream,
+                      reference=vlb.VLB_REF_REST if rf == "rest" else vlb.VLB_REF_UNIFORM)
+        m0 = sim.moments(fields=False)["mass"]
+        sim.step(drift_steps)
+        m1 = sim.moments(fields=False)["mass"]
+        sim.close()
+        res["mass_drift"] = {"steps": drift_steps, "relative": float(m1 / m0 - 1.0)}
+        out[name] = res
+    oracle = None
+    if orc is not None:
+        oracle = {"file": os.path.relpath(ref_path, ROOT), "steps": marks,
+                  "mass_drift": {"steps": marks[-1], "relative": float(orc["mass_%d" % marks[-1]] / orc["mass0"] - 1.0)}}
+    return {"instance": "channel_d3q19_64^3 (stretch 0.7, bump 0.05 h, tau 0.8, body force 1e-5, "
+                        "seeded 1% noise, seed 3)",
+            "checkpoints": marks, "metrics": "rho_abs = max|rho - rho_ref|; u_rel = max|u - u_ref| / max|u_ref|",
+            "oracle": oracle if oracle is not None else "absent (run tests/golden/precision_reference.py)",
+            "forms": out}
+
+
+def bench_precision(a):
+    """The storage-precision forms: throughput of FP32, FP16 and BF16 (rest
+    reference, FP32 arithmetic) on the --n^3 channel of the headline workload
+    (default 384^3), timed the same way in the same run, and their accuracy
+    and mass drift (precision_accuracy)."""
+    import torch
+
+    from paper_2401_17183_gb300 import build as B
+    B.build()
+    from paper_2401_17183_gb300 import vlb
+    from paper_2401_17183_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    n = a.n
+    mesh = W.channel_mesh(n, n, n, stretch=a.stretch, bump=a.bump)
+    prm = W.params(a.tau, body_force=(1e-6, 0.0, 0.0))
+    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
+    gm = vlb.Mesh(mesh)
+    del mesh
+    ncell = n ** 3
+    peak, peak_kind = measured_peak_hbm()
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    thr = {}
+    for st in ("f32", "f16", "bf16"):
+        p = {"f32": vlb.VLB_F32, "f16": vlb.VLB_F16, "bf16": vlb.VLB_BF16}[st]
+        sim = vlb.Sim(gm, prm, rho, u, precision=p, stream=stream.cuda_stream,
+                      reference=vlb.VLB_REF_REST if st != "f32" else vlb.VLB_REF_UNIFORM)
+        ms = time_steps(sim, a.steps, a.warmup, stream)
+        sim.close()
+        bpc = BYTES_PER_CELL[("19", st)]
+        ach = bpc * ncell / (ms / 1e3 / a.steps) / 1e9
+        thr[st] = {"value": ncell * a.steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / a.steps,
+                   "reference": "rest" if st != "f32" else "uniform", "bytes_per_cell_update": bpc,
+                   "achieved_gbs": ach, "frac": ach / peak}
+    clocks = sampler.stop()
+    del gm
+    acc = precision_accuracy(stream, a.drift_steps)
+    line = {
+        "metric": "MLUPS of the 16-bit storage forms (FP32 arithmetic) and their error against the FP64 GPU "
+                  "path and the oracle", "value": thr["f16"]["value"], "unit": "MLUPS",
+        "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": thr["f16"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 storage, f32 arithmetic", "data": "synthetic (seeded mesh and 1% velocity noise)",
+        "config": {"workload": "channel_d3q19_%d^3_precision_forms" % n, "cells": ncell, "lattice": "D3Q19",
+                   "stretch": a.stretch, "bump": a.bump, "tau": a.tau, "body_force": 1e-6,
+                   "l2": "no flush: populations >= %.2f GB > 129 MB L2" % (ncell * 19 * 2 / 1e9)},
+        "throughput": thr, "peak": peak, "peak_kind": peak_kind, "clocks": clocks,
+        "f16_over_f32": thr["f16"]["value"] / thr["f32"]["value"], "accuracy": acc,
+        "gpu_launches": 3 * a.steps,
+    }
+    print(json.dumps(line))
+
+
 def warmstart_leg(ntrain, ntest, iters):
     """Steps and wall time to a 1e-6 residual from the learned prediction and
     from rest, on held-out members of the bumped 2D channel family."""
@@ -538,6 +702,8 @@ def main():
         return bench_warmstart(a)
     if a.workload == "d3q39":
         return bench_d3q39(a)
+    if a.workload == "precision":
+        return bench_precision(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -669,7 +835,10 @@ def main():
                "phases_s": {"reset": t1 - t0, "steps": ms / 1e3, "moments_kernels": t5 - t4,
                             "fields_d2h": max(0.0, (t3 - t1) - ms / 1e3 - (t5 - t4))}}
 
-    general = tts = None
+    general = tts = s16 = None
+    if a.mesh == "channel" and a.storage == "f32" and world == 1 and not a.no_storage16:
+        # the FP16-storage form of the same workload (rest reference)
+        s16 = storage16_leg(a, gmesh, prm, rho, u, stream)
     if a.general_n > 0 and a.mesh == "channel" and a.storage == "f32" and world == 1:
         del sim, gmesh
         general = general_mesh_leg(a, stream)
@@ -696,7 +865,7 @@ def main():
                                                         "bf16": "__nv_bfloat16"}[a.storage],
                      "source_sha": source_sha()},
         "clocks": clocks, "e2e": e2e, "gpu_launches": a.steps, "cpu_baseline": cpu,
-        "general_mesh": general, "time_to_steady": tts,
+        "storage16": s16, "general_mesh": general, "time_to_steady": tts,
     }
     print(json.dumps(line))
     if world > 1:

@@ -20,7 +20,7 @@ template <int Q>
 constexpr bool record_pairs_aligned() {
   using L = vlb::CoefLayout<Q>;
   constexpr int D = L::D;
-  bool ok = L::template stride<float>() % 4 == 0 && L::ROWN % 4 == 0 && L::MPD % 4 == 0 &&
+  bool ok = L::template stride<float>() % 4 == 0 && L::SREST % 4 == 0 && L::MPD % 4 == 0 &&
             L::QM % 4 == 0 && L::HM % 2 == 0;
   // 16-byte quads of the link coefficients, 8-byte component-2 pairs
   for (int p = 1; p <= L::H; p++) ok = ok && L::mp(p, 0) % 4 == 0 && (D == 2 || L::mp(p, 2) % 2 == 0);

@@ -279,8 +279,11 @@ struct MomentWeights<9, R> {
 // T_lk = T0_l + 3 C2h^kl (a direction with components on l and k):
 //   axis e_l: xo / 3 = c^l T0_l;   diagonal: xo / 3 = c^l T_lk + c^k T_kl,
 // and the even part of a diagonal is Bh_ll + Bh_kk - tr Bh / 3 + 2 c^l c^k Bh_lk.
-template <int Q, typename R>
-__device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ rc, R m, R mdev,
+// mn = m - J is the mass of the flow. With REST the populations come in, and
+// go out, relative to the cell's own rest state already (d_a = n_a, and
+// dp_a = N'_a - o_a), so the subtraction of the rest deviation drops out.
+template <int Q, typename R, bool REST>
+__device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ rc, R m, R mn,
                                         R h2m, R rho, R itau, const R (&U)[Lat<Q>::D],
                                         const R (&Phi)[Lat<Q>::D], R (&dp)[Q]) {
   using L = CoefLayout<Q>;
@@ -409,11 +412,10 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
   const R a9_1 = (R(9) * lat_w<Q, R>(1)) * J, a9_2 = (R(9) * lat_w<Q, R>(Lat<Q>::H)) * J;
   const R tr3 = tr * R(1.0 / 3.0);
   const R b3_1 = a9_1 * tr3, b3_2 = a9_2 * tr3;
-  // m - J, the mass of the flow
-  const R mn = mdev - rc[L::RR + H + 1];
   {
     const R w = lat_w<Q, R>(0);
-    const R neq = ((d[0] - rc[L::RR]) - rc[L::RW] * mn) - (R(3) * w * m) * xe[0];
+    const R n0 = REST ? d[0] : d[0] - rc[L::RR];
+    const R neq = (n0 - rc[L::RW] * mn) - (R(3) * w * m) * xe[0];
     dp[0] = d[0] - itau * neq - (R(3) * w * J) * tr;
   }
   const R wm1 = MW::a1 * m, wm2 = MW::a2 * m;
@@ -437,12 +439,12 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
     const R Ep = fmar(axis ? a9_1 : a9_2, cPc, -(axis ? b3_1 : b3_2));
     const R Op = (axis ? MW::a1 : MW::a2) * cF;
     const R wm = axis ? wm1 : wm2;
-    const R r0 = rc[L::RR + p], rw = rc[L::RW + p];
+    const R rw = rc[L::RW + p];
     // odd part of J f^eq over 3 w: m xo on diagonals, m O on axis pairs
     if constexpr (sizeof(R) == 4) {
       // the pair in the two lanes of packed FP32 instructions (same roundings)
       const float2 dd = make_float2(d[p], d[p + H]);
-      const float2 bs = __ffma2_rn(bcast2(-rw), bcast2(mn), __fadd2_rn(dd, bcast2(-r0)));
+      const float2 bs = __ffma2_rn(bcast2(-rw), bcast2(mn), REST ? dd : __fadd2_rn(dd, bcast2(-rc[L::RR + p])));
       float2 nq;
       if (axis) {
         const R o = sl > 0 ? Oax[l] : -Oax[l];
@@ -458,6 +460,7 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
       dp[p + H] = r.y;
     } else {
       R neqp, neqm;
+      const R r0 = REST ? R(0) : rc[L::RR + p];
       const R bp = fmar(-rw, mn, d[p] - r0), bm = fmar(-rw, mn, d[p + H] - r0);
       if (axis) {
         const R o = sl > 0 ? Oax[l] : -Oax[l];
@@ -481,8 +484,9 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
 // size, so smaller changes are rounding noise. With FINAL, the post-collision
 // deviations are formed at the converged Phi.
 // rc points at the cell's coefficient record (global, shared or local
-// memory); itau = 1/tau.
-template <int Q, typename R, bool FINAL>
+// memory); itau = 1/tau. With REST, d holds e_a = N_a - o_a relative to the
+// cell's own rest state (16-bit storage, see CoefLayout), and so does dp.
+template <int Q, typename R, bool FINAL, bool REST = false>
 __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restrict__ rc, R nref,
                                              R itau, R tol, int max_iter, R (&dp)[Q],
                                              CollideState<Q, R> &st) {
@@ -491,6 +495,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
   static_assert(D == 2 || NQ % 4 == 0, "row 2 of the chord step is read in 16-byte quads");
   const R epsn = sizeof(R) == 4 ? R(64.0 / 16777216.0) : R(64.0 / 9007199254740992.0);
   // pair sums s_p = d_p + d_pbar and differences t_p = d_p - d_pbar
+  // (with REST: of e_a; the rest state's part of the s_p enters through SR)
   R sp[H + 1], tp[H + 1];
   R mdev = d[0];
 #pragma unroll
@@ -498,6 +503,14 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     sp[p] = d[p] + d[p + H];
     tp[p] = d[p] - d[p + H];
     mdev += sp[p];
+  }
+  // m - J, the mass of the flow
+  R mn;
+  if constexpr (REST) {
+    mn = mdev + rc[L::MNV];
+    mdev += rc[L::MDV];
+  } else {
+    mn = mdev - rc[L::RR + H + 1];
   }
   const R m = nref + mdev;
   // rho = sum f = sum N / J; rho U = sum c f   (Eqs. 14, 15, 17)
@@ -531,6 +544,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     pr[i] = nref * kw;
     const R err = two_prod_err(nref, kw, pr[i]) + nref * rc[L::KWL + i];
     s[i] = m * rc[L::BODY + i] - err - R(0.5) * itau * mdev * kw;
+    if constexpr (REST) s[i] += rc[L::SR + i];
   }
   if constexpr (sizeof(R) == 4) {
     // components 0 and 1 in the two lanes of packed FP32 instructions, two
@@ -669,7 +683,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     }
   }
   st.iters = it;
-  if (FINAL) form_np<Q, R>(d, rc, m, mdev, h2m, st.rho, itau, st.U, Phi, dp);
+  if (FINAL) form_np<Q, R, REST>(d, rc, m, mn, h2m, st.rho, itau, st.U, Phi, dp);
 #pragma unroll
   for (int i = 0; i < D; i++) st.F[i] = Phi[i] * rc[L::IJ];
 }

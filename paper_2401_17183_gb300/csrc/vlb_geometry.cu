@@ -368,14 +368,25 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
     }
     rec[L::RR + H + 1] = rsum;
   }
-  // storage references: the rest state of Eq. 33 at the column that holds each
-  // location, as offsets from the uniform reference (the fastest axis never
-  // changes the column, so only the other axes decide a wall crossing)
+  // 16-bit storage relative to the rest state of Eq. 33 at the column that
+  // holds each location (the fastest axis never changes the column, so only
+  // the other axes decide a wall crossing): the constants and the per-link
+  // column differences that let the collision work on N_a - o_a(own)
   if (a.ref_rest) {
     const Addr<Q> ad0(a.g, c);
+    double own[Q], osum = 0.0;
     for (int av = 0; av < Q; av++) {
-      const double wn = lat_w<Q, double>(av) * a.nref;
-      rec[L::ROWN + av] = rest_ref<Q>(a.J[c], a.ginv + c * NS, av) - wn;
+      own[av] = rest_ref<Q>(a.J[c], a.ginv + c * NS, av);
+      osum += own[av];
+    }
+    rec[L::MDV] = osum - a.nref;   // the weights sum to one
+    rec[L::MNV] = osum - a.J[c];
+    for (int i = 0; i < D; i++) {
+      double s = 0.0;
+      for (int p = 1; p <= H; p++) s += rec[L::mp(p, i)] * 2.0 * (own[p] - lat_w<Q, double>(p) * a.nref);
+      rec[L::SR + i] = s;
+    }
+    for (int av = 0; av < Q; av++) {
       for (int sg = -1; sg <= 1; sg += 2) {
         bool crs = false;
         for (int ax = 0; ax < D - 1; ax++) {
@@ -383,7 +394,11 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
           if ((cd > 0 && ad0.hi[ax]) || (cd < 0 && ad0.lo[ax])) crs = true;
         }
         const int64_t cb = crs || av == 0 ? c : (ad0.nb(av, sg) / a.nfast) * a.nfast;
-        rec[(sg < 0 ? L::RIN : L::ROUT) + av] = rest_ref<Q>(a.J[cb], a.ginv + cb * NS, av) - wn;
+        const double ob = rest_ref<Q>(a.J[cb], a.ginv + cb * NS, av);
+        if (sg < 0)
+          rec[L::DIN + av] = ob - own[av];
+        else
+          rec[L::DOUT + av] = own[av] - ob;
       }
     }
   }

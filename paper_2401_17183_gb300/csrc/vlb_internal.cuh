@@ -152,15 +152,28 @@ struct CoefLayout {
   // state, w_p (1 + x_p)
   static constexpr int RR = round4(QM + D * NQ);
   static constexpr int RW = RR + round4(H + 2);
-  // storage references of 16-bit populations (reference VLB_REF_REST, plane
-  // mode), as offsets from the uniform reference, r - w_a n_ref: at the cell's
-  // own locations, at the location each population of an odd step is read
-  // from (slot abar of q - c_a), and at the one it is written to (slot a of
-  // q + c_a); a link through a wall reads and writes the cell's own slot
-  static constexpr int ROWN = round4(RW + H + 1);
-  static constexpr int RIN = ROWN + Q;
-  static constexpr int ROUT = RIN + Q;
-  static constexpr int NC = ROUT + Q;
+  // 16-bit populations relative to the rest state (reference VLB_REF_REST,
+  // plane mode). A location (slot, cell) holding a population of direction a
+  // stores N_a - o_a, o_a = J w_a (1 + x_a) of the column that holds the
+  // location, rounded to FP32 (even in the direction). The collision then
+  // works on e_a = N_a - o_a(own column) directly; it needs
+  //   SR + i  sum_p am M^i_p 2 (o_p - w_p n_ref), the part of the pair sums
+  //           of the deviations that the rest state carries,
+  //   MDV     sum_a (o_a - w_a n_ref), so that m - n_ref = sum_a e_a + MDV,
+  //   MNV     sum_a o_a - J, so that m - J = sum_a e_a + MNV,
+  // and, for odd steps, the differences to the columns that a population is
+  // read from (slot abar of q - c_a) and written to (slot a of q + c_a):
+  //   DIN + a   o_a(column of q - c_a) - o_a(own),
+  //   DOUT + a  o_a(own) - o_a(column of q + c_a),
+  // both zero for a link through a wall (the cell's own slot). Kernels that
+  // do not read 16-bit rest-relative populations stage the record up to SREST.
+  static constexpr int SREST = round4(RW + H + 1);
+  static constexpr int SR = SREST;
+  static constexpr int MDV = SR + D;
+  static constexpr int MNV = MDV + 1;
+  static constexpr int DIN = round4(MNV + 1);
+  static constexpr int DOUT = DIN + Q;
+  static constexpr int NC = DOUT + Q;
   __host__ __device__ static constexpr int mp(int p, int i) {
     return i < 2 ? MPD + 4 * (p - 1) + i : MPD + 4 * H + 2 * (p - 1);
   }

@@ -28,8 +28,9 @@
 // reading tile k + 2 ahead of the writes of tile k is safe.
 //
 // Populations may be stored in 16 bits (IEEE half or bfloat16) with FP32
-// arithmetic: each value is staged as the aligned 32-bit word that contains
-// it and the thread remembers which half it is.
+// arithmetic: on even steps of full tiles the row segments are staged as
+// they are; otherwise each value is staged as the aligned 32-bit word that
+// contains it and the thread remembers which half it is.
 #pragma once
 
 #include <mutex>
@@ -128,12 +129,22 @@ __device__ __forceinline__ IT src_index(IT ps, const Addr<Q, IT> &ad, int a) {
   return (IT)lat_opp<Q>(a) * ps + ad.nb(a, -1);
 }
 
+// does c_a move along a slow axis (and so, in plane mode, to another column)?
+template <int Q>
+__host__ __device__ constexpr bool slow_move(int a) {
+  bool m = false;
+  for (int d = 0; d < Lat<Q>::D - 1; d++) m = m || Lat<Q>::c(a, d) != 0;
+  return m;
+}
+
 // resident blocks per SM the register budget is cut for: 3 for FP32
 // arithmetic (168 registers, no spills; 4 blocks at 128 registers ran 0.5%
-// slower, 5 at 102 registers 18% slower), 2 for FP64
-template <typename R>
+// slower, 5 at 102 registers 18% slower), 4 for the even steps of 16-bit
+// storage (128 registers without spills, 3% faster than 3 blocks; their odd
+// steps took the same time at 4 blocks with 4% more instructions), 2 for FP64
+template <typename R, typename S = R, bool ODD = false>
 constexpr int step_min_blocks() {
-  return sizeof(R) == 4 ? 3 : 2;
+  return sizeof(R) == 4 ? (sizeof(S) == 2 && !ODD ? 4 : 3) : 2;
 }
 
 // pipeline depth: tiles whose copies are in flight while one is collided
@@ -165,8 +176,10 @@ __device__ __forceinline__ __nv_bfloat16 s16_from_bits<__nv_bfloat16>(unsigned s
   return __ushort_as_bfloat16(b);
 }
 
-// REFOFS: 16-bit populations stored relative to the local rest state (the
-// offsets from the uniform reference come with the record, plane mode only).
+// REFOFS: 16-bit populations stored relative to the rest state of the column
+// that holds them (plane mode only); the collision works on them relative to
+// its own column's rest state, so even steps add no offsets at all and odd
+// steps add the record's column differences on links that change column.
 // HPAR: 16-bit storage with an even cell count and an even fastest axis, so
 // that which half of its 32-bit word a value sits in follows from the cell's
 // own parity: a neighbour along a slow axis (or behind a wall: the own cell)
@@ -182,7 +195,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
   static_assert(!REFOFS || (PLANE && H16), "storage offsets need plane mode and 16-bit storage");
   static_assert(!HPAR || H16, "half parity applies to 16-bit storage");
   // 16-byte pieces of the record that the kernel reads
-  constexpr int RCHUNK = (REFOFS ? RS : L::ROWN) * (int)sizeof(R) / 16;
+  constexpr int RCHUNK = (REFOFS ? RS : L::SREST) * (int)sizeof(R) / 16;
   static_assert(RCHUNK <= kStepThreads, "record larger than one copy per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<Q, S, R> &sm = *reinterpret_cast<StepSmem<Q, S, R> *>(smem_raw);
@@ -203,7 +216,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
   auto prefetch = [&](const TileCursor &c, int st) {
     const IT ifast = (IT)c.tf * kStepThreads + (IT)tid;
     bool rows = false;
-    if constexpr (!ODD && !H16) {
+    if constexpr (!ODD) {
       if (a.full_tiles) {
         rows = true;
         const IT cell0 = tile_addr<Q, IT>(a.g, c, (IT)c.tf * kStepThreads).cell;
@@ -218,10 +231,21 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
     if (!rows && ifast < nfast) {
       const Addr<Q, IT> ad = tile_addr<Q, IT>(a.g, c, ifast);
       if constexpr (H16 && HPAR) {
+        // the same neighbour arithmetic on 32-bit words: the slow-axis moves
+        // are even, the fastest-axis move is the cell's own word difference
+        Addr<Q, IT> adw = ad;
+        adw.cell = ad.cell >> 1;
+#pragma unroll
+        for (int d = 0; d < D - 1; d++) {
+          adw.dp[d] = ad.dp[d] / 2;
+          adw.dm[d] = ad.dm[d] / 2;
+        }
+        adw.dp[D - 1] = ((ad.cell + ad.dp[D - 1]) >> 1) - adw.cell;
+        adw.dm[D - 1] = ((ad.cell + ad.dm[D - 1]) >> 1) - adw.cell;
 #pragma unroll
         for (int av = 0; av < Q; av++)
           cp_async<4>(&sm.pop[st][av][tid],
-                      reinterpret_cast<const uint32_t *>(f) + (src_index<Q, ODD, IT>(ps, ad, av) >> 1));
+                      reinterpret_cast<const uint32_t *>(f) + src_index<Q, ODD, IT>(ps / 2, adw, av));
       } else if constexpr (H16) {
         uint32_t hi = 0;
 #pragma unroll
@@ -280,25 +304,56 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
 
       R N[Q];
       if constexpr (H16) {
-        const uint32_t hi = HPAR ? 0u : sm.half_hi[st][tid];
-        // HPAR: the shift of the own cell's half and of the other one
-        const unsigned sh0 = ((unsigned)cell & 1u) << 4, sh1 = 16u - sh0;
+        if (!ODD && a.full_tiles) {
+          // the tile's row segments, 16 bits per cell
 #pragma unroll
-        for (int av = 0; av < Q; av++) {
-          const uint32_t w = sm.pop[st][av][tid];
-          unsigned short b;
-          if constexpr (HPAR) {
-            const bool shifted = ODD && Lat<Q>::c(av, D - 1) != 0 && !ad.crosses(av, -1);
-            b = (unsigned short)(w >> (shifted ? sh1 : sh0));
-          } else {
-            b = (unsigned short)(((hi >> av) & 1) ? (w >> 16) : (w & 0xffffu));
-          }
-          N[av] = load_s<R>(s16_from_bits<S>(b));
-          if constexpr (REFOFS) {
-            // back to the uniform reference: add the storage offset of the location
-            const bool own = !ODD || av == 0 || ad.crosses(av, -1);
-            N[av] += rc[(own ? L::ROWN : L::RIN) + av];
-          }
+          for (int av = 0; av < Q; av++)
+            N[av] = load_s<R>(s16_from_bits<S>(reinterpret_cast<const unsigned short *>(&sm.pop[st][av][0])[tid]));
+        } else {
+          const uint32_t hi = HPAR ? 0u : sm.half_hi[st][tid];
+          // HPAR: the shift of the own cell's half and of the other one
+          const unsigned sh0 = ((unsigned)cell & 1u) << 4, sh1 = 16u - sh0;
+          auto unpack = [&](auto inner_tag) {
+            constexpr bool INNER = decltype(inner_tag)::value;
+#pragma unroll
+            for (int av = 0; av < Q; av++) {
+              const uint32_t w = sm.pop[st][av][tid];
+              unsigned short b;
+              if constexpr (HPAR) {
+                // away from walls every move along the fastest axis reads the
+                // other half; a link through a wall reads the own cell
+                const bool shifted = ODD && Lat<Q>::c(av, D - 1) != 0 && (INNER || !ad.crosses(av, -1));
+                b = (unsigned short)(w >> (shifted ? sh1 : sh0));
+              } else {
+                b = (unsigned short)(((hi >> av) & 1) ? (w >> 16) : (w & 0xffffu));
+              }
+              N[av] = load_s<R>(s16_from_bits<S>(b));
+            }
+          };
+          // a tile away from every wall (uniform over the tile): the halves
+          // follow from the cell parity alone
+          bool inner = ODD && HPAR && !a.g.wall[D - 1];
+#pragma unroll
+          for (int d = 0; d < D - 1; d++) inner = inner && !ad.lo[d] && !ad.hi[d];
+          if (inner)
+            unpack(std::true_type());
+          else
+            unpack(std::false_type());
+        }
+        if constexpr (REFOFS && ODD) {
+          // relative to the own column's rest state: a population read from a
+          // neighbouring column carries that column's storage reference. The
+          // record's differences are zero where a slow-axis wall sends the link
+          // back to the own slot; a fastest-axis wall does so only at the ends
+          // of a row, which the masks take care of.
+          const R mlo = ad.lo[D - 1] ? R(0) : R(1), mhi = ad.hi[D - 1] ? R(0) : R(1);
+#pragma unroll
+          for (int av = 1; av < Q; av++)
+            if (slow_move<Q>(av)) {
+              const int cz = Lat<Q>::c(av, D - 1);
+              const R dv = rc[L::DIN + av];
+              N[av] = cz == 0 ? N[av] + dv : fmar(dv, cz > 0 ? mlo : mhi, N[av]);
+            }
         }
       } else {
 #pragma unroll
@@ -308,7 +363,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
       // ---- collide (section 2.2)
       R Np[Q];
       CollideState<Q, R> cst;
-      collide_cell<Q, R, true>(N, rc, arg_r<R>(a.nref, a.nref_f), arg_r<R>(a.itau, a.itau_f),
+      collide_cell<Q, R, true, REFOFS>(N, rc, arg_r<R>(a.nref, a.nref_f), arg_r<R>(a.itau, a.itau_f),
                                      arg_r<R>(a.tol, a.tol_f), a.max_iter, Np, cst);
       if (!cst.conv) atomicOr(a.err, ERR_NOCONV);
 
@@ -342,12 +397,18 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
         const int ab = lat_opp<Q>(av);
         const bool crs = ad.crosses(av, 1);
         R v = Np[av];
-        if constexpr (REFOFS) v -= rc[((!ODD || crs) ? L::ROWN : L::ROUT) + av];
+        if constexpr (REFOFS && ODD) {
+          if (slow_move<Q>(av)) {
+            const int cz = Lat<Q>::c(av, D - 1);
+            const R dv = rc[L::DOUT + av];
+            v = cz == 0 ? v + dv : fmar(dv, cz > 0 ? (ad.hi[D - 1] ? R(0) : R(1)) : (ad.lo[D - 1] ? R(0) : R(1)), v);
+          }
+        }
         // one store through a selected index (own slot abar, or slot a of q + c_a)
         const IT idx = (!ODD || crs) ? (IT)ab * ps + cell : (IT)av * ps + ad.nb(av, 1);
         f[idx] = store_s<S>(v);
       }
-      f[cell] = store_s<S>(REFOFS ? Np[0] - rc[L::ROWN] : Np[0]);
+      f[cell] = store_s<S>(Np[0]);
     }
     cur.next(a);
     if (++st == kStages) st = 0;
@@ -357,7 +418,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
 
 // One mesh: block b walks the tiles [b per_block, (b + 1) per_block).
 template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, bool HPAR, typename IT>
-__global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>())
+__global__ void __launch_bounds__(kStepThreads, step_min_blocks<R, S, ODD>())
     k_step(const __grid_constant__ StepArgs a) {
   const int64_t t0 = (int64_t)blockIdx.x * a.per_block;
   const int64_t t1 = t0 + a.per_block < a.ntiles ? t0 + a.per_block : a.ntiles;

@@ -233,3 +233,17 @@ def params(tau, body_force=(0.0, 0.0, 0.0), wall_u=None, wall_omega=None, max_it
             "wall_u": None if wall_u is None else np.asarray(wall_u, dtype=np.float64),
             "wall_omega": None if wall_omega is None else np.asarray(wall_omega, dtype=np.float64),
             "max_iter": int(max_iter), "tol": float(tol)}
+
+
+# --------------------------------------------------------------------------- instances
+
+def precision_instance(n=64):
+    """The storage-precision comparison instance: the channel family of the
+    headline workload (tanh stretching 0.7, lower-wall bump 0.05 h) at n^3
+    cells, tau = 0.8, body force 1e-5 streamwise (a channel flow of about
+    0.01 after 1000 steps on top of the decaying noise), rho = 1 and seeded
+    1% velocity noise. Returns (mesh, params, rho, u)."""
+    mesh = channel_mesh(n, n, n, stretch=0.7, bump=0.05)
+    prm = params(0.8, body_force=(1e-5, 0.0, 0.0))
+    rho, u = noise_fields(mesh, amp=0.01, seed=3)
+    return mesh, prm, rho, u
