@@ -44,8 +44,10 @@ BYTES_PER_CELL = {("19", "f32"): 2 * 19 * 4, ("19", "f64"): 2 * 19 * 8, ("9", "f
                   ("9", "f64"): 2 * 9 * 8, ("19", "f16"): 2 * 19 * 2, ("19", "bf16"): 2 * 19 * 2}
 STEP_SOURCES = ["vlb_step.cu", "vlb_step.cuh", "vlb_collide.cuh", "vlb_addr.cuh", "vlb_internal.cuh"]
 # the coefficient record values the D3Q19 FP32 step kernel reads per cell
-# (CoefLayout<19>::SREST: everything before the 16-bit rest-relative block)
-RECORD_FLOATS_READ = 172
+# with one record per cell (CoefLayout<19>::RR: everything before the rest
+# state, which that mode forms from J and g^ij; the wall velocity after it is
+# read in moving-wall cells only)
+RECORD_FLOATS_READ = 136
 
 
 def args_parse():

@@ -20,7 +20,8 @@ template <int Q>
 constexpr bool record_pairs_aligned() {
   using L = vlb::CoefLayout<Q>;
   constexpr int D = L::D;
-  bool ok = L::template stride<float>() % 4 == 0 && L::SREST % 4 == 0 && L::MPD % 4 == 0 &&
+  bool ok = L::template stride<float, true>() % 4 == 0 && L::template stride<float, false>() % 4 == 0 &&
+            L::SREST % 4 == 0 && L::MPD % 4 == 0 && L::UW + D <= L::RR &&
             L::QM % 4 == 0 && L::HM % 2 == 0;
   // 16-byte quads of the link coefficients, 8-byte component-2 pairs
   for (int p = 1; p <= L::H; p++) ok = ok && L::mp(p, 0) % 4 == 0 && (D == 2 || L::mp(p, 2) % 2 == 0);
@@ -334,8 +335,10 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
     s->ref_rest = 1;
   }
   const bool f64 = vlb::arith_f64(params->precision);
-  s->nc = q == 9    ? (f64 ? vlb::CoefLayout<9>::stride<double>() : vlb::CoefLayout<9>::stride<float>())
-          : q == 19 ? (f64 ? vlb::CoefLayout<19>::stride<double>() : vlb::CoefLayout<19>::stride<float>())
+  using L9 = vlb::CoefLayout<9>;
+  using L19 = vlb::CoefLayout<19>;
+  s->nc = q == 9    ? (plane ? L9::stride<float, true>() : L9::stride<float, false>())
+          : q == 19 ? (plane ? L19::stride<float, true>() : L19::stride<float, false>())
                     : 0;  // D3Q39: no records, the kernels read the mesh geometry
   if (q == VLB_D3Q39) s->ncoef = 0;
   const size_t es = f64 ? 8 : 4;

@@ -80,7 +80,7 @@ __device__ void inverse_small(const double (&A)[D][D], double (&X)[D][D]) {
 
 // Coefficient record of one cell in FP64 from its geometry: J, g^ij (packed),
 // G^i = G . g^i and the link coefficients K^i_a (Eq. 25). Every entry is
-// filled except FR and UW, which are left zero. With itau = 1/tau,
+// filled except FR, the rest state and UW, which are left zero. With itau = 1/tau,
 // cpi = -(1 - itau/2) and the pair sums over p = 1..H:
 //   R^i_kl  = sum_p w_p M^i_p (3 c^k_p c^l_p - delta_kl)
 //   Ao^i_p  = w_p [itau D^i_p + 3 cpi c_p.R^i.M_p]    (xo_p: BGK part and, via S, E_p)
@@ -115,10 +115,7 @@ __device__ void build_record(double J, const double *ginv, const double *G,
   for (int i = 0; i < D; i++)
     for (int j = 0; j < D; j++) gd[i][j] = ginv[sym<D>(i, j)] - (i == j ? 1.0 : 0.0);
   for (int i = 0; i < D; i++)
-    for (int j = i; j < D; j++) {
-      rec[L::GINV + sym<D>(i, j)] = gd[i][j];
-      rec[L::GH + sym<D>(i, j)] = 0.5 * gd[i][j];
-    }
+    for (int j = i; j < D; j++) rec[L::GH + sym<D>(i, j)] = 0.5 * gd[i][j];
   for (int i = 0; i < D; i++) {
     rec[L::BODY + i] = G[i];
     double s = 0.0;
@@ -282,15 +279,63 @@ struct MomentWeights<9, R> {
 // mn = m - J is the mass of the flow. With REST the populations come in, and
 // go out, relative to the cell's own rest state already (d_a = n_a, and
 // dp_a = N'_a - o_a), so the subtraction of the rest deviation drops out.
-template <int Q, typename R, bool REST>
-__device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ rc, R m, R mn,
-                                        R h2m, R rho, R itau, const R (&U)[Lat<Q>::D],
+// With RREC the rest state comes from the record (RR, RW); otherwise it is
+// formed here from J and Gh = (g - I)/2, x^0_p / 3 = c_p.Gh.c_p - tr Gh / 3:
+//   RW_p = w_p + 3 w_p (x^0_p / 3),  RR_p = w_p (J - n_ref) + 3 w_p J (x^0_p / 3),
+// and then mn = mdev - sum_a RR_a. Every term is formed relative to its own
+// size, and the identity behind the final pass holds for whatever J it uses,
+// as long as RR, their sum and mn use the same one.
+template <int Q, typename R, bool REST, bool RREC>
+__device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ rc, R m, R mdev, R mn,
+                                        R nref, R h2m, R rho, R itau, const R (&U)[Lat<Q>::D],
                                         const R (&Phi)[Lat<Q>::D], R (&dp)[Q]) {
   using L = CoefLayout<Q>;
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H, NS = L::NS;
+  static_assert(RREC || !REST, "rest-relative storage keeps the rest state in the record");
   R gh[NS];
 #pragma unroll
   for (int i = 0; i < NS; i++) gh[i] = rc[L::GH + i];
+  R rwc[RREC ? 1 : H + 1], rrc[RREC ? 1 : H + 1];
+  if constexpr (!RREC) {
+    const R Jc = rc[L::J], Jd = Jc - nref;
+    R trg = gh[sym<D>(0, 0)];
+#pragma unroll
+    for (int i = 1; i < D; i++) trg += gh[sym<D>(i, i)];
+    const R tr3 = trg * R(1.0 / 3.0);
+    R rsum = R(0);
+#pragma unroll
+    for (int p = 0; p <= H; p++) {
+      R t;
+      if (p == 0) {
+        t = -tr3;
+      } else {
+        const int l = nz_axis<Q>(p, 0), k = nz_axis<Q>(p, 1);
+        if (k < 0) {
+          t = gh[sym<D>(l, l)] - tr3;
+        } else {
+          const int sg = Lat<Q>::c(p, l) * Lat<Q>::c(p, k);
+          t = fmar(R(2 * sg), gh[sym<D>(l, k)], gh[sym<D>(l, l)] + gh[sym<D>(k, k)]) - tr3;
+        }
+      }
+      const R w = lat_w<Q, R>(p), w3 = R(3) * w;
+      rwc[p] = fmar(w3, t, w);
+      rrc[p] = fmar(w3 * Jc, t, w * Jd);
+      rsum += p == 0 ? rrc[p] : R(2) * rrc[p];
+    }
+    mn = mdev - rsum;
+  }
+  auto rw_at = [&](int p) -> R {
+    if constexpr (RREC)
+      return rc[L::RW + p];
+    else
+      return rwc[p];
+  };
+  auto rr_at = [&](int p) -> R {
+    if constexpr (RREC)
+      return rc[L::RR + p];
+    else
+      return rrc[p];
+  };
   const R hh = R(0.5) * h2m;
   R Ut[D], Uh[D], U2[D], Ut2x[D], v[D];
 #pragma unroll
@@ -414,8 +459,8 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
   const R b3_1 = a9_1 * tr3, b3_2 = a9_2 * tr3;
   {
     const R w = lat_w<Q, R>(0);
-    const R n0 = REST ? d[0] : d[0] - rc[L::RR];
-    const R neq = (n0 - rc[L::RW] * mn) - (R(3) * w * m) * xe[0];
+    const R n0 = REST ? d[0] : d[0] - rr_at(0);
+    const R neq = (n0 - rw_at(0) * mn) - (R(3) * w * m) * xe[0];
     dp[0] = d[0] - itau * neq - (R(3) * w * J) * tr;
   }
   const R wm1 = MW::a1 * m, wm2 = MW::a2 * m;
@@ -439,12 +484,12 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
     const R Ep = fmar(axis ? a9_1 : a9_2, cPc, -(axis ? b3_1 : b3_2));
     const R Op = (axis ? MW::a1 : MW::a2) * cF;
     const R wm = axis ? wm1 : wm2;
-    const R rw = rc[L::RW + p];
+    const R rw = rw_at(p);
     // odd part of J f^eq over 3 w: m xo on diagonals, m O on axis pairs
     if constexpr (sizeof(R) == 4) {
       // the pair in the two lanes of packed FP32 instructions (same roundings)
       const float2 dd = make_float2(d[p], d[p + H]);
-      const float2 bs = __ffma2_rn(bcast2(-rw), bcast2(mn), REST ? dd : __fadd2_rn(dd, bcast2(-rc[L::RR + p])));
+      const float2 bs = __ffma2_rn(bcast2(-rw), bcast2(mn), REST ? dd : __fadd2_rn(dd, bcast2(-rr_at(p))));
       float2 nq;
       if (axis) {
         const R o = sl > 0 ? Oax[l] : -Oax[l];
@@ -460,7 +505,7 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
       dp[p + H] = r.y;
     } else {
       R neqp, neqm;
-      const R r0 = REST ? R(0) : rc[L::RR + p];
+      const R r0 = REST ? R(0) : rr_at(p);
       const R bp = fmar(-rw, mn, d[p] - r0), bm = fmar(-rw, mn, d[p + H] - r0);
       if (axis) {
         const R o = sl > 0 ? Oax[l] : -Oax[l];
@@ -486,7 +531,7 @@ __device__ __forceinline__ void form_np(const R (&d)[Q], const R *__restrict__ r
 // rc points at the cell's coefficient record (global, shared or local
 // memory); itau = 1/tau. With REST, d holds e_a = N_a - o_a relative to the
 // cell's own rest state (16-bit storage, see CoefLayout), and so does dp.
-template <int Q, typename R, bool FINAL, bool REST = false>
+template <int Q, typename R, bool FINAL, bool REST = false, bool RREC = true>
 __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restrict__ rc, R nref,
                                              R itau, R tol, int max_iter, R (&dp)[Q],
                                              CollideState<Q, R> &st) {
@@ -510,7 +555,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     mn = mdev + rc[L::MNV];
     mdev += rc[L::MDV];
   } else {
-    mn = mdev - rc[L::RR + H + 1];
+    mn = RREC ? mdev - rc[L::RR + H + 1] : R(0);   // else formed in form_np
   }
   const R m = nref + mdev;
   // rho = sum f = sum N / J; rho U = sum c f   (Eqs. 14, 15, 17)
@@ -683,7 +728,7 @@ __device__ __forceinline__ void collide_cell(const R (&d)[Q], const R *__restric
     }
   }
   st.iters = it;
-  if (FINAL) form_np<Q, R, REST>(d, rc, m, mn, h2m, st.rho, itau, st.U, Phi, dp);
+  if (FINAL) form_np<Q, R, REST, RREC>(d, rc, m, mdev, mn, nref, h2m, st.rho, itau, st.U, Phi, dp);
 #pragma unroll
   for (int i = 0; i < D; i++) st.F[i] = Phi[i] * rc[L::IJ];
 }

@@ -322,7 +322,6 @@ template <int Q, typename R>
 __global__ void k_pack_coef(const PackArgs a, R *coef) {
   constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
-  constexpr int RS = L::template stride<R>();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= a.nrec) return;
   const int64_t c = a.plane ? r * a.nfast : r;
@@ -338,7 +337,7 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
   // F at rest (rho = 1, U = 0), the start value of the chord iteration
   {
     double gd[NS], U0[D], N[Q], Np[Q];
-    for (int i = 0; i < NS; i++) gd[i] = rec[L::GINV + i];
+    for (int i = 0; i < NS; i++) gd[i] = 2.0 * rec[L::GH + i];
     for (int i = 0; i < D; i++) U0[i] = 0.0;
     EqParts<Q, double> e;
     eq_parts<Q, double>(gd, U0, U0, e);
@@ -355,7 +354,7 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
   // reference, their sum over all directions, and the rest weights
   {
     double gd[NS], U0[D], rsum = 0.0;
-    for (int i = 0; i < NS; i++) gd[i] = rec[L::GINV + i];
+    for (int i = 0; i < NS; i++) gd[i] = 2.0 * rec[L::GH + i];
     for (int i = 0; i < D; i++) U0[i] = 0.0;
     EqParts<Q, double> e;
     eq_parts<Q, double>(gd, U0, U0, e);
@@ -402,8 +401,9 @@ __global__ void k_pack_coef(const PackArgs a, R *coef) {
       }
     }
   }
-  R *out = coef + r * RS;
-  for (int k = 0; k < RS; k++) out[k] = k < L::NC ? static_cast<R>(rec[k]) : R(0);
+  // a per-cell record ends at RR (see CoefLayout::stride)
+  R *out = coef + r * a.stride;
+  for (int k = 0; k < a.stride; k++) out[k] = k < L::NC ? static_cast<R>(rec[k]) : R(0);
   // reference-state part of J F as a hi/lo pair
   for (int i = 0; i < D; i++) {
     const R hi = static_cast<R>(rec[L::KW + i]);
@@ -448,7 +448,7 @@ static cudaError_t pack_q(const vlb_sim *sim, cudaStream_t s) {
   a.ginv = m->d_ginv;
   a.K = m->d_K;
   a.nrec = sim->ncoef;
-  a.stride = 0;
+  a.stride = sim->nc;
   a.nfast = m->md.n[m->md.dim - 1];
   a.plane = sim->plane;
   a.tau = sim->p.tau;

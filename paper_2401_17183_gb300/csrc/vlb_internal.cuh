@@ -122,14 +122,12 @@ struct CoefLayout {
   static constexpr int NQ = NS + NO;           // monomials of U~ in one chord step
   // set-up of a collision
   static constexpr int J = 0;                  // J (Eq. 5)
-  static constexpr int GINV = 1;               // g^ij - delta^ij packed (Eq. 8)
-  static constexpr int GH = GINV + NS;         // (g^ij - delta^ij) / 2 packed
+  static constexpr int GH = 1;                 // (g^ij - delta^ij) / 2 packed (Eq. 8)
   static constexpr int BODY = GH + NS;         // G^i = G . g^i
   static constexpr int KW = BODY + D;          // sum_a w_a K^i_a (reference-state part of J F)
   static constexpr int KWL = KW + D;           // its low part: KW + KWL = the FP64 value
   static constexpr int FR = KWL + D;           // F of the rest state at rho = 1 (start value)
-  static constexpr int UW = FR + D;            // wall velocity U_w^i (wall cells)
-  static constexpr int CE = UW + D;            // constant term of the map
+  static constexpr int CE = FR + D;            // constant term of the map
   static constexpr int PO1 = CE + D;           // D x D: coefficient of U (row-major)
   static constexpr int IJ = PO1 + D * D;       // 1 / J
   // link coefficients (see above)
@@ -149,9 +147,18 @@ struct CoefLayout {
   // RR + p (p = 0..H) its deviation from the uniform reference,
   // J w_p (1 + x_p) - w_p n_ref (even in the direction), RR + H + 1 the sum of
   // those deviations over all Q directions, and RW + p the weight of the rest
-  // state, w_p (1 + x_p)
+  // state, w_p (1 + x_p). Both follow from J and g^ij; with one record per
+  // cell the step recomputes them rather than streaming them (see
+  // rest_state), so a per-cell record is read up to RR only.
   static constexpr int RR = round4(QM + D * NQ);
   static constexpr int RW = RR + round4(H + 2);
+  // wall velocity U_w^i (read in the wall cells of moving walls only), in the
+  // padding after the chord matrix or after the map coefficients, so that a
+  // per-cell record ends at RR
+  static constexpr int UW = QM - (HM + D * D) >= D   ? HM + D * D
+                            : RR - (QM + D * NQ) >= D ? QM + D * NQ
+                                                      : -1;
+  static_assert(UW >= 0, "no padding gap holds the wall velocity");
   // 16-bit populations relative to the rest state (reference VLB_REF_REST,
   // plane mode). A location (slot, cell) holding a population of direction a
   // stores N_a - o_a, o_a = J w_a (1 + x_a) of the column that holds the
@@ -181,10 +188,13 @@ struct CoefLayout {
     return i < 2 ? MPD + 4 * (p - 1) + 2 + i : MPD + 4 * H + 2 * (p - 1) + 1;
   }
   // record stride in elements of type R: a multiple of four elements, so that
-  // every record and group starts on a 16-byte boundary
-  template <typename R>
+  // every record and group starts on a 16-byte boundary. One record per
+  // column (PLANE) holds everything; one record per cell ends at RR (the rest
+  // state is formed from J and g^ij, the 16-bit rest-relative block needs
+  // plane mode), which for D3Q19 FP32 is 544 bytes, 17 whole 32-byte sectors.
+  template <typename R, bool PLANE = true>
   static constexpr int stride() {
-    return round4(NC);
+    return PLANE ? round4(NC) : RR;
   }
 };
 

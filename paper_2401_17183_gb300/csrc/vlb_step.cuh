@@ -156,7 +156,7 @@ constexpr int kStages = 3;
 // 4, 8 or 16 bytes), with one bit per direction saying which half it is.
 template <int Q, typename S, typename R>
 struct StepSmem {
-  static constexpr int RS = CoefLayout<Q>::template stride<R>();
+  static constexpr int RS = CoefLayout<Q>::template stride<R, true>();
   static constexpr bool H16 = sizeof(S) == 2;
   using PopT = typename std::conditional<H16, uint32_t, S>::type;
   alignas(16) R rec[kStages][RS];
@@ -190,7 +190,7 @@ template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, bool
 __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, const int64_t t1) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
-  constexpr int RS = L::template stride<R>();
+  constexpr int RS = L::template stride<R, PLANE>();
   constexpr bool H16 = sizeof(S) == 2;
   static_assert(!REFOFS || (PLANE && H16), "storage offsets need plane mode and 16-bit storage");
   static_assert(!HPAR || H16, "half parity applies to 16-bit storage");
@@ -314,7 +314,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
           // HPAR: the shift of the own cell's half and of the other one
           const unsigned sh0 = ((unsigned)cell & 1u) << 4, sh1 = 16u - sh0;
           auto unpack = [&](auto inner_tag) {
-            constexpr bool INNER = decltype(inner_tag)::value;
+            [[maybe_unused]] constexpr bool INNER = decltype(inner_tag)::value;
 #pragma unroll
             for (int av = 0; av < Q; av++) {
               const uint32_t w = sm.pop[st][av][tid];
@@ -363,7 +363,8 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
       // ---- collide (section 2.2)
       R Np[Q];
       CollideState<Q, R> cst;
-      collide_cell<Q, R, true, REFOFS>(N, rc, arg_r<R>(a.nref, a.nref_f), arg_r<R>(a.itau, a.itau_f),
+      // (with one record per cell the rest state is formed, not read)
+      collide_cell<Q, R, true, REFOFS, PLANE>(N, rc, arg_r<R>(a.nref, a.nref_f), arg_r<R>(a.itau, a.itau_f),
                                      arg_r<R>(a.tol, a.tol_f), a.max_iter, Np, cst);
       if (!cst.conv) atomicOr(a.err, ERR_NOCONV);
 
@@ -378,7 +379,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
           zero[i] = R(0);
         }
 #pragma unroll
-        for (int i = 0; i < L::NS; i++) gd[i] = rc[L::GINV + i];
+        for (int i = 0; i < L::NS; i++) gd[i] = R(2) * rc[L::GH + i];
         EqParts<Q, R> ew;
         eq_parts<Q, R>(gd, uw, zero, ew);
         const R Jr2 = R(2) * rc[L::J] * cst.rho;
