@@ -390,9 +390,6 @@ def bench_batch(a):
                             precision=vlb.VLB_F32, stream=stream.cuda_stream))
     ncell = sum(W.ncell(m) for m in meshes)
     batch = vlb.Batch(sims)
-    run = batch.tune(4)
-    batch.step(a.warmup)
-    torch.cuda.synchronize()
 
     def timed(fn):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -402,6 +399,20 @@ def bench_batch(a):
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
+
+    # every block shape at its default run length (for the record), then the
+    # tuner's choice of shape and run length
+    shapes, k_shape = [], max(32, a.steps // 4)
+    for i in range(4):
+        batch.set_shape(i)
+        batch.step(a.warmup)
+        ms_i = timed(lambda: batch.step(k_shape))
+        ly = batch.layout()
+        shapes.append({"threads": ly["threads"], "min_blocks_per_sm": ly["min_blocks"],
+                       "tiles_per_block": ly["run_length"], "value": ncell * k_shape / (ms_i / 1e3) / 1e6})
+    run = batch.tune(4)
+    batch.step(a.warmup)
+    torch.cuda.synchronize()
 
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
     ms = timed(lambda: batch.step(a.steps))
@@ -426,10 +437,12 @@ def bench_batch(a):
         "config": {"workload": "batch_%d_channel2d_d2q9_fp32" % a.nmesh, "meshes": a.nmesh, "cells": ncell,
                    "sizes": "streamwise log-uniform 64..512, wall-normal half", "tau": a.tau,
                    "blocks_per_launch": lay["blocks"], "tiles_per_block": run,
+                   "threads_per_block": lay["threads"], "min_blocks_per_sm": lay["min_blocks"],
                    "graph": "32 launches per CUDA graph"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "bytes_per_cell_update": bpc},
+        "shapes_at_default_run": shapes,
         "one_launch_per_mesh": {"value": alone, "unit": "MLUPS", "steps": k_alone,
                                 "speedup_of_batch": value / alone},
         "clocks": clocks, "gpu_launches": a.steps,

@@ -215,8 +215,8 @@ const char *vlb_last_error(void);
  * Each member's time step is the same fused stream-and-collide of Eq. 12 /
  * Eq. 22 as vlb_step (the per-cell arithmetic is identical, so a batch gives
  * bit-for-bit the populations of stepping each member alone). The members'
- * tiles (128 cells along the fastest axis) are cut into runs and every run is
- * one block of a single launch; a member's work thus never waits for a launch
+ * tiles (128 or, after vlb_batch_tune, possibly 64 cells along the fastest
+ * axis) are cut into runs and every run is one block of a single launch; a member's work thus never waits for a launch
  * of its own, which is what pays for many small meshes.
  *   sims    nsims >= 1 simulations on the current device with the same
  *           lattice, precision (VLB_F32 or VLB_F64), coefficient mode (all
@@ -230,10 +230,27 @@ int vlb_batch_create(vlb_sim *const *sims, int32_t nsims, vlb_batch **out);
  * errors raised by kernels are sticky per member, see vlb_sync). Whole runs
  * of 32 steps replay a CUDA graph of 32 launches built on first use. */
 int vlb_batch_step(vlb_batch *b, int64_t nsteps);
-/* Pick the run length (tiles per block) by timing: each of a few candidates
- * runs `steps` steps on the members (the simulations advance by
- * 4 * steps in total). Blocks until done. run_length_out may be NULL. */
+/* Pick the block shape and the run length (tiles per block) by timing. The
+ * shapes are the tile width (threads per block, cells along the fastest
+ * axis: 128 or 64; narrow tiles waste fewer threads at the ragged end of
+ * short rows) with the resident blocks per SM that the registers are cut
+ * for (four shapes for VLB_F32 members, two for VLB_F64); with each shape,
+ * run lengths of about 1, 2, 4 and 8 runs per resident block. Every
+ * candidate runs `steps` steps on the members, so the simulations advance by
+ * the count vlb_batch_tune_steps gives. Blocks until done. run_length_out
+ * may be NULL. */
 int vlb_batch_tune(vlb_batch *b, int32_t steps, int64_t *run_length_out);
+/* The number of steps vlb_batch_tune(b, steps, ...) advances every member by. */
+int vlb_batch_tune_steps(const vlb_batch *b, int32_t steps, int64_t *advanced);
+/* Use block shape `shape` (0 .. 3 for VLB_F32 members, 0 .. 1 for VLB_F64, in
+ * the order 128 threads with the single-mesh step's register budget, 128
+ * with a smaller one, then the same two budgets at 64 threads) with its
+ * default run length, about two runs per resident block. EINVAL outside
+ * that range. */
+int vlb_batch_set_shape(vlb_batch *b, int32_t shape);
+/* The block shape in use: threads per block (= tile width) and the resident
+ * blocks per SM its kernel's registers were cut for. Either may be NULL. */
+int vlb_batch_shape(const vlb_batch *b, int32_t *threads, int32_t *min_blocks);
 /* Blocks (tile runs) per launch and tiles per run; for reporting. */
 int vlb_batch_layout(const vlb_batch *b, int64_t *blocks, int64_t *run_length, int64_t *cells);
 void vlb_batch_destroy(vlb_batch *b);

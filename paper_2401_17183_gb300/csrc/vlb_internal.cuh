@@ -457,6 +457,8 @@ struct vlb_batch {
   size_t items_cap = 0;
   cudaGraphExec_t graph = nullptr;  // 32 launches, even parity first
   int64_t graph_run = 0;      // run length the graph was built for
+  int32_t shape = 0;          // block shape (index into the batch's shape table)
+  int32_t graph_shape = -1;   // shape the graph was built for
 };
 
 namespace vlb {

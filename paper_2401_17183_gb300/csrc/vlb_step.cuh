@@ -154,14 +154,15 @@ constexpr int kStages = 3;
 // in plane mode, the coefficient record they all share. A 16-bit population
 // is staged as the aligned 32-bit word that holds it (asynchronous copies move
 // 4, 8 or 16 bytes), with one bit per direction saying which half it is.
-template <int Q, typename S, typename R>
+// T is the tile width (threads per block).
+template <int Q, typename S, typename R, int T = kStepThreads>
 struct StepSmem {
   static constexpr int RS = CoefLayout<Q>::template stride<R, true>();
   static constexpr bool H16 = sizeof(S) == 2;
   using PopT = typename std::conditional<H16, uint32_t, S>::type;
   alignas(16) R rec[kStages][RS];
-  PopT pop[kStages][Q][kStepThreads];
-  uint32_t half_hi[H16 ? kStages : 1][kStepThreads];
+  PopT pop[kStages][Q][T];
+  uint32_t half_hi[H16 ? kStages : 1][T];
 };
 
 // a 16-bit storage value from its bit pattern
@@ -185,8 +186,10 @@ __device__ __forceinline__ __nv_bfloat16 s16_from_bits<__nv_bfloat16>(unsigned s
 // own parity: a neighbour along a slow axis (or behind a wall: the own cell)
 // has the same parity, one along the fastest axis (periodic wrap included:
 // nfast - 1 is odd) the other one.
-// The tiles [t0, t1) of one mesh, as one block.
-template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, bool HPAR, typename IT>
+// The tiles [t0, t1) of one mesh, as one block of T threads (tiles of T
+// cells; the arguments' tile counts must be those of width T).
+template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, bool HPAR, typename IT,
+          int T = kStepThreads>
 __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, const int64_t t1) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
   using L = CoefLayout<Q>;
@@ -196,9 +199,8 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
   static_assert(!HPAR || H16, "half parity applies to 16-bit storage");
   // 16-byte pieces of the record that the kernel reads
   constexpr int RCHUNK = (REFOFS ? RS : L::SREST) * (int)sizeof(R) / 16;
-  static_assert(RCHUNK <= kStepThreads, "record larger than one copy per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StepSmem<Q, S, R> &sm = *reinterpret_cast<StepSmem<Q, S, R> *>(smem_raw);
+  StepSmem<Q, S, R, T> &sm = *reinterpret_cast<StepSmem<Q, S, R, T> *>(smem_raw);
   S *__restrict__ f = static_cast<S *>(a.f);
   const R *__restrict__ coef = static_cast<const R *>(a.coef);
   const IT ps = (IT)a.ncell;
@@ -206,7 +208,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
   const int tid = threadIdx.x;
 
   // pieces of 16 bytes in one direction's row segment of a tile
-  constexpr int PER_ROW = kStepThreads * (int)sizeof(S) / 16;
+  constexpr int PER_ROW = T * (int)sizeof(S) / 16;
 
   // issue this thread's copies for tile c into stage st: the populations of
   // its cell and, in plane mode, one 16-byte piece of the shared record. On
@@ -214,14 +216,14 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
   // segment, so the block copies the Q segments in 16-byte pieces instead
   // (thread tid takes pieces tid, tid + 128, ...).
   auto prefetch = [&](const TileCursor &c, int st) {
-    const IT ifast = (IT)c.tf * kStepThreads + (IT)tid;
+    const IT ifast = (IT)c.tf * T + (IT)tid;
     bool rows = false;
     if constexpr (!ODD) {
       if (a.full_tiles) {
         rows = true;
-        const IT cell0 = tile_addr<Q, IT>(a.g, c, (IT)c.tf * kStepThreads).cell;
+        const IT cell0 = tile_addr<Q, IT>(a.g, c, (IT)c.tf * T).cell;
 #pragma unroll
-        for (int k = tid; k < Q * PER_ROW; k += kStepThreads) {
+        for (int k = tid; k < Q * PER_ROW; k += T) {
           const int av = k / PER_ROW, j = k - av * PER_ROW;
           cp_async<16>(reinterpret_cast<unsigned char *>(&sm.pop[st][av][0]) + 16 * j,
                        reinterpret_cast<const unsigned char *>(f + ((IT)av * ps + cell0)) + 16 * j);
@@ -261,10 +263,12 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
           cp_async<sizeof(S)>(&sm.pop[st][av][tid], f + src_index<Q, ODD, IT>(ps, ad, av));
       }
     }
-    if (PLANE && tid < RCHUNK) {
+    if constexpr (PLANE) {
       const int64_t rec = (int64_t)c.A * a.nB + c.B;
-      cp_async<16>(reinterpret_cast<unsigned char *>(&sm.rec[st][0]) + 16 * tid,
-                   reinterpret_cast<const unsigned char *>(coef + rec * RS) + 16 * tid);
+      // one piece per thread, or several where the block is narrower
+      for (int k = tid; k < RCHUNK; k += T)
+        cp_async<16>(reinterpret_cast<unsigned char *>(&sm.rec[st][0]) + 16 * k,
+                     reinterpret_cast<const unsigned char *>(coef + rec * RS) + 16 * k);
     }
   };
 
@@ -293,7 +297,7 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
       nxt.next(a);
     }
 
-    const IT ifast = (IT)cur.tf * kStepThreads + (IT)tid;
+    const IT ifast = (IT)cur.tf * T + (IT)tid;
     if (ifast < nfast) {
       const Addr<Q, IT> ad = tile_addr<Q, IT>(a.g, cur, ifast);
       const IT cell = ad.cell;
@@ -435,16 +439,19 @@ struct BatchItem {
   int64_t t0, t1;
 };
 
-template <int Q, typename S, typename R, bool ODD, bool PLANE, typename IT>
-__global__ void __launch_bounds__(kStepThreads, step_min_blocks<R>())
+// T threads per block (the tile width) and at least MINB resident blocks per
+// SM (which caps the registers per thread): the batch's block shape.
+template <int Q, typename S, typename R, bool ODD, bool PLANE, typename IT, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB)
     k_step_batch(const StepArgs *__restrict__ args, const BatchItem *__restrict__ items) {
   const BatchItem it = items[blockIdx.x];
-  step_tiles<Q, S, R, ODD, PLANE, false, false, IT>(args[it.sim], it.t0, it.t1);
+  step_tiles<Q, S, R, ODD, PLANE, false, false, IT, T>(args[it.sim], it.t0, it.t1);
 }
 
-// Arguments of one simulation's step kernel (per_block left for the caller).
+// Arguments of one simulation's step kernel for tiles of T cells (per_block
+// left for the caller).
 template <int Q>
-inline StepArgs make_step_args(const vlb_sim *sim) {
+inline StepArgs make_step_args(const vlb_sim *sim, int T = kStepThreads) {
   const vlb_mesh *m = sim->mesh;
   StepArgs a;
   a.f = sim->d_f;
@@ -468,18 +475,18 @@ inline StepArgs make_step_args(const vlb_sim *sim) {
         if (sim->p.wall_u[ax][sd][d] != 0.0 || sim->p.wall_omega[ax][sd][d] != 0.0) a.moving = 1;
   const int dim = m->md.dim;
   const int64_t nfast = dim == 3 ? m->md.n[2] : m->md.n[1];
-  a.ntf = (int32_t)((nfast + kStepThreads - 1) / kStepThreads);
+  a.ntf = (int32_t)((nfast + T - 1) / T);
   a.nA = (int32_t)(dim == 3 ? m->md.n[0] : 1);
   a.nB = (int32_t)(dim == 3 ? m->md.n[1] : m->md.n[0]);
   a.ntiles = (int64_t)a.ntf * a.nA * a.nB;
   a.per_block = 0;
-  a.full_tiles = nfast % kStepThreads == 0 ? 1 : 0;
+  a.full_tiles = nfast % T == 0 ? 1 : 0;
   return a;
 }
 
 // blocks the persistent kernel can keep resident on the current device
 // (queried once per kernel and device)
-static int resident_blocks(const void *kern, size_t smem) {
+static int resident_blocks(const void *kern, size_t smem, int threads = kStepThreads) {
   static std::mutex mu;
   static std::vector<std::tuple<const void *, int, int>> cache;
   int dev = 0;
@@ -489,7 +496,7 @@ static int resident_blocks(const void *kern, size_t smem) {
     if (std::get<0>(e) == kern && std::get<1>(e) == dev) return std::get<2>(e);
   int nb = 0, nsm = 0;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStepThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int total = (nb > 0 ? nb : 1) * (nsm > 0 ? nsm : 1);
   cache.emplace_back(kern, dev, total);

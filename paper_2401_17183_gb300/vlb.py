@@ -85,6 +85,9 @@ def load():
         "vlb_batch_create": ([C.POINTER(vp), C.c_int32, C.POINTER(vp)], C.c_int),
         "vlb_batch_step": ([vp, C.c_int64], C.c_int),
         "vlb_batch_tune": ([vp, C.c_int32, C.POINTER(C.c_int64)], C.c_int),
+        "vlb_batch_tune_steps": ([vp, C.c_int32, C.POINTER(C.c_int64)], C.c_int),
+        "vlb_batch_shape": ([vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
+        "vlb_batch_set_shape": ([vp, C.c_int32], C.c_int),
         "vlb_batch_layout": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                               C.POINTER(C.c_int64)], C.c_int),
         "vlb_batch_destroy": ([vp], None),
@@ -297,10 +300,22 @@ class Batch:
         _check(load().vlb_batch_tune(self.h, int(steps), C.byref(r)), "vlb_batch_tune")
         return r.value
 
+    def set_shape(self, shape):
+        _check(load().vlb_batch_set_shape(self.h, int(shape)), "vlb_batch_set_shape")
+
+    def tune_steps(self, steps=10):
+        """How many steps tune(steps) advances every member by."""
+        r = C.c_int64()
+        _check(load().vlb_batch_tune_steps(self.h, int(steps), C.byref(r)), "vlb_batch_tune_steps")
+        return r.value
+
     def layout(self):
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         _check(load().vlb_batch_layout(self.h, C.byref(a), C.byref(b), C.byref(c)), "vlb_batch_layout")
-        return {"blocks": a.value, "run_length": b.value, "cells": c.value}
+        th, mb = C.c_int32(), C.c_int32()
+        _check(load().vlb_batch_shape(self.h, C.byref(th), C.byref(mb)), "vlb_batch_shape")
+        return {"blocks": a.value, "run_length": b.value, "cells": c.value, "threads": th.value,
+                "min_blocks": mb.value}
 
     def close(self):
         if getattr(self, "h", None):

@@ -72,13 +72,32 @@ def test_batch_from_odd_parity_and_tuner(V):
     for s in alone + batched:
         s.step(1)
     b = V.Batch(batched)
-    run = b.tune(3)                 # advances every member by 4 x 3 steps
-    assert run >= 1 and b.layout()["run_length"] == run
+    adv = b.tune_steps(3)
+    run = b.tune(3)                 # every block shape and run length, 3 steps each
+    lay = b.layout()
+    assert run >= 1 and lay["run_length"] == run
+    assert adv == 4 * 4 * 3 and lay["threads"] in (64, 128)
     b.step(40)
     for s in alone:
-        s.step(12 + 40)
+        s.step(adv + 40)
     for s, t in zip(alone, batched):
-        assert t.time() == s.time() == 53
+        assert t.time() == s.time() == 1 + adv + 40
+        assert np.array_equal(s.get_state(), t.get_state())
+
+
+@pytest.mark.parametrize("shape", range(4))
+def test_batch_every_block_shape_matches_individual_steps(V, shape):
+    """Each block shape the tuner may pick (tile width 128 or 64, two register
+    budgets) gives the members' own steps bit for bit, ragged rows included."""
+    alone, batched = _channels(V), _channels(V)
+    b = V.Batch(batched)
+    b.set_shape(shape)
+    assert b.layout()["threads"] == (128 if shape < 2 else 64)
+    for s in alone:
+        s.step(37)
+    b.step(37)                      # one 32-step graph replay and a remainder
+    for s, t in zip(alone, batched):
+        t.sync()
         assert np.array_equal(s.get_state(), t.get_state())
 
 
