@@ -218,91 +218,81 @@ def cpu_model():
     return info
 
 
-def _oracle_replica(job):
-    """One oracle run on its own sample (a spawned process): returns the
-    seconds of the timed steps."""
-    n, steps, warmup, tau, stretch, bump = job
-    sys.path.insert(0, ROOT)
+def _oracle_sample(n, tau, stretch, bump):
     from oracle import OracleSim
     from paper_2401_17183_gb300 import workloads as W
     mesh = W.channel_mesh(*n, stretch=stretch, bump=bump)
     rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
     o = OracleSim(mesh, W.params(tau, body_force=(1e-6, 0.0, 0.0)))
     o.init(rho, u)
-    o.step(warmup)
+    return o
+
+
+def _oracle_timed(o, min_steps, min_s, max_steps=200):
+    """Steps of a running oracle until both min_steps and min_s are reached."""
     t = time.perf_counter()
-    o.step(steps)
-    return time.perf_counter() - t
-
-
-def oracle_on_cores(n, steps, warmup, tau, stretch, bump, procs):
-    """The oracle as it stands on `procs` host cores at once: independent
-    replicas of the same sample in spawned processes (no shared state, no
-    change to the oracle). Returns (aggregate MLUPS, slowest replica's seconds)."""
-    import multiprocessing as mp
-    ctx = mp.get_context("spawn")
-    job = (n, steps, warmup, tau, stretch, bump)
-    with ctx.Pool(procs) as pool:
-        secs = pool.map(_oracle_replica, [job] * procs)
-    cells = n[0] * n[1] * n[2]
-    return procs * cells * steps / max(secs) / 1e6, max(secs)
+    k = 0
+    while k < min_steps or (time.perf_counter() - t < min_s and k < max_steps):
+        o.step(1)
+        k += 1
+    return k, time.perf_counter() - t
 
 
 def reference_sample_run(steps, warmup, tau, stretch, bump, budget_s=120.0):
-    """The FP64 oracle on all host cores (one replica per core), on a bounded
-    sample of the channel family sized so that the run fits budget_s."""
-    from oracle import OracleSim
-    from paper_2401_17183_gb300 import workloads as W
-    prm = W.params(tau, body_force=(1e-6, 0.0, 0.0))
-    mesh = W.channel_mesh(6, 6, 6, stretch=stretch, bump=bump)
-    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
-    o = OracleSim(mesh, prm)
-    o.init(rho, u)
-    t = time.perf_counter()
-    o.step(1)
-    per_cell = (time.perf_counter() - t) / 216
-    per_step_budget = budget_s / max(1, steps + warmup)
-    s = 4
-    while (s + 2) ** 3 * per_cell <= per_step_budget and s < 32:
-        s += 2
+    """The FP64 oracle as it stands, its time step on every host core
+    (OpenMP over the cells), on a bounded sample of the channel family sized
+    so that warmup + steps fit budget_s."""
+    from oracle import set_threads
     cpu = cpu_model()
     procs = max(1, int(cpu["cpus"] or 1))
-    value, el = oracle_on_cores((s, s, s), steps, warmup, tau, stretch, bump, procs)
-    return {"value": value, "cells": s ** 3, "steps": steps, "seconds": el, "cores": procs, "cpu": cpu,
+    set_threads(procs)
+    o = _oracle_sample((8, 8, 8), tau, stretch, bump)
+    t = time.perf_counter()
+    o.step(1)
+    per_cell = (time.perf_counter() - t) / 512
+    per_step_budget = budget_s / max(1, steps + warmup)
+    s = 8
+    while (s + 4) ** 3 * per_cell <= per_step_budget and s < 48:
+        s += 4
+    o = _oracle_sample((s, s, s), tau, stretch, bump)
+    o.step(warmup)
+    t = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t
+    return {"value": s ** 3 * steps / el / 1e6, "cells": s ** 3, "steps": steps, "seconds": el, "cores": procs,
+            "cpu": cpu,
             "sample": "%d^3 cells of the same channel family (stretch %g, bump %g h, walls, body force, "
-                      "tau %g), %d timed steps, one independent replica per core on %d cores"
-                      % (s, stretch, bump, tau, steps, procs)}
+                      "tau %g), %d timed steps, OpenMP over the cells on %d cores" % (s, stretch, bump, tau, steps, procs)}
 
 
 def cpu_baseline_leg(tau, stretch, bump):
     """Oracle MLUPS on a bounded sample (32 x 32 x 16 cells of the channel
-    family): single-threaded, and on every host core at once (one replica per
-    core, spawned processes); about 10-20 s of CPU work each."""
-    from oracle import OracleSim
-    from paper_2401_17183_gb300 import workloads as W
-    prm = W.params(tau, body_force=(1e-6, 0.0, 0.0))
+    family), its time step on every host core (OpenMP over the cells) and on
+    one thread; at least 10 s of stepping each (the single-thread leg) or
+    3 s (all cores)."""
+    from oracle import set_threads
     n = (32, 32, 16)
-    mesh = W.channel_mesh(*n, stretch=stretch, bump=bump)
-    rho, u = W.noise_fields(mesh, amp=0.01, seed=2)
-    o = OracleSim(mesh, prm)
-    o.init(rho, u)
-    o.step(1)
-    t = time.perf_counter()
-    k = 0
-    while k < 3 or (time.perf_counter() - t < 10.0 and k < 200):
-        o.step(1)
-        k += 1
-    el = time.perf_counter() - t
     nc = n[0] * n[1] * n[2]
-    single = nc * k / el / 1e6
     cpu = cpu_model()
     procs = max(1, int(cpu["cpus"] or 1))
-    allc, el_all = oracle_on_cores(n, k, 1, tau, stretch, bump, procs)
-    return {"value": allc, "unit": "MLUPS", "cores": procs, "kind": "oracle", "cpu": cpu,
+    before = set_threads(0)
+    try:
+        set_threads(1)
+        o = _oracle_sample(n, tau, stretch, bump)
+        o.step(1)
+        k1, el1 = _oracle_timed(o, 3, 10.0)
+        set_threads(procs)
+        o = _oracle_sample(n, tau, stretch, bump)
+        o.step(1)
+        kp, elp = _oracle_timed(o, 10, 3.0, 2000)
+    finally:
+        set_threads(before)
+    return {"value": nc * kp / elp / 1e6, "unit": "MLUPS", "cores": procs, "kind": "oracle", "cpu": cpu,
             "sample": "32x32x16 cells of the same channel family (D3Q19, FP64, stretch %g, bump %g h, "
-                      "tau %g), %d steps; one independent replica per core on %d cores (%.1f s)"
-                      % (stretch, bump, tau, k, procs, el_all),
-            "single_thread": {"value": single, "unit": "MLUPS", "cores": 1, "seconds": el}}
+                      "tau %g), %d steps with OpenMP over the cells on %d cores (%.1f s)"
+                      % (stretch, bump, tau, kp, procs, elp),
+            "single_thread": {"value": nc * k1 / el1 / 1e6, "unit": "MLUPS", "cores": 1, "steps": k1,
+                              "seconds": el1}}
 
 
 def general_mesh_leg(a, stream):

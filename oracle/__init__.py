@@ -4,4 +4,4 @@ TEST INFRASTRUCTURE: imported only by tests/, __graft_entry__.smoke() and the
 CPU-baseline leg of bench.py. The product package never imports it.
 """
 from .vlbo import (OracleSim, cell_geometry, collide, equilibrium, lattice, load,  # noqa: F401
-                   position)
+                   position, set_threads)

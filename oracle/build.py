@@ -1,8 +1,9 @@
 """Compile the FP64 CPU oracle (test infrastructure) into oracle/liboracle_vlb.so.
 
 Plain gcc, -O2 with floating-point contraction off so every product and sum
-rounds as written. Host-portable: no -march flags, builds the same on x86-64
-and aarch64.
+rounds as written, and OpenMP for the loop over the cells of a step (each
+cell's arithmetic is the same on any number of threads). Host-portable: no
+-march flags, builds the same on x86-64 and aarch64.
 """
 import os
 import subprocess
@@ -15,7 +16,7 @@ HDR = os.path.join(HERE, "vlb_oracle.h")
 
 def _cc(out, src):
     tmp = out + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-Wall", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-Wall", "-fPIC", "-shared", "-fopenmp",
            "-I", HERE, "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)

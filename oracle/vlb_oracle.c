@@ -7,6 +7,9 @@
  * the way it is written.  No blocking, fusion or reordering: each function
  * evaluates one equation of the paper, in its notation, with explicit loops.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "vlb_oracle.h"
 
 #include <math.h>
@@ -576,22 +579,47 @@ int vlbo_init(vlbo_sim *s, const double *rho, const double *u) {
   return VLBO_OK;
 }
 
+int vlbo_set_threads(int32_t n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
+/* One time step per pass over the cells. Each cell reads only its own
+ * arrived populations and writes each of its post-collision populations to a
+ * location no other cell writes, so the cells may be taken by several
+ * threads (OpenMP) with results identical bit for bit to one thread; a
+ * failed solve is reported for the lowest failing cell index. */
 int vlbo_step(vlbo_sim *s, int64_t nsteps) {
   int q = s->m.q, D = s->m.dim;
   const int32_t(*c)[3] = lat_c(q);
   int64_t nc = s->ncell;
   int32_t maxit = 0;
   for (int64_t t = 0; t < nsteps; t++) {
+    int32_t stepit = 0;
+    int64_t bad = -1;
+    int badrc = 0;
+#pragma omp parallel for schedule(static) reduction(max : stepit)
     for (int64_t k = 0; k < nc; k++) {
       const vlbo_cell *cl = &s->cells[k];
       double N[VLBO_QMAX], Np[VLBO_QMAX];
       for (int a = 0; a < q; a++) N[a] = s->N[a * nc + k];
       int32_t it = 0;
       int rc = vlbo_collide(q, cl, &s->p, N, Np, NULL, NULL, NULL, NULL, NULL, &it);
-      if (it > maxit) maxit = it;
+      if (it > stepit) stepit = it;
       if (rc) {
-        s->last_iters = maxit;
-        return rc;
+#pragma omp critical(vlbo_step_error)
+        {
+          if (bad < 0 || k < bad) {
+            bad = k;
+            badrc = rc;
+          }
+        }
+        continue;
       }
       double rho = 0.0;
       for (int a = 0; a < q; a++) rho += N[a] / cl->J;
@@ -618,6 +646,11 @@ int vlbo_step(vlbo_sim *s, int64_t nsteps) {
         }
         s->Nn[a * nc + node_index(&s->m, p)] = Np[a];
       }
+    }
+    if (stepit > maxit) maxit = stepit;
+    if (bad >= 0) {
+      s->last_iters = maxit;
+      return badrc;
     }
     double *tmp = s->N;
     s->N = s->Nn;

@@ -130,7 +130,12 @@ int vlbo_create(const vlbo_mesh *m, const vlbo_params *p, vlbo_sim **out);
 void vlbo_destroy(vlbo_sim *s);
 /* N_a = J f^eq_a(rho, U, U~ = U) with U^i = u . g^i; rho [ncell], u [ncell][dim]. */
 int vlbo_init(vlbo_sim *s, const double *rho, const double *u);
+/* nsteps time steps; the cells of a step may run on several threads
+ * (OpenMP), with the same result bit for bit as on one. */
 int vlbo_step(vlbo_sim *s, int64_t nsteps);
+/* Threads vlbo_step may use from now on in this process (n <= 0 leaves the
+ * setting); returns the count in effect (1 without OpenMP). */
+int vlbo_set_threads(int32_t n);
 /* rho [ncell], u and u_tilde [ncell][dim] (Euclidean, Eq. 34 with U and U~),
  * F [ncell][dim] index components, totals[7] = mass, P (3), M (3). */
 int vlbo_moments(vlbo_sim *s, double *rho, double *u, double *u_tilde, double *F,

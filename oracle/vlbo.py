@@ -73,6 +73,8 @@ def _configure(lib):
     lib.vlbo_get_cell.argtypes = [C.c_void_p, C.c_int64, C.POINTER(_Cell)]
     lib.vlbo_last_iters.argtypes = [C.c_void_p]
     lib.vlbo_last_iters.restype = C.c_int32
+    lib.vlbo_set_threads.argtypes = [C.c_int32]
+    lib.vlbo_set_threads.restype = C.c_int
     return lib
 
 
@@ -81,6 +83,13 @@ def load():
     if _lib is None:
         _lib = _configure(C.CDLL(build_oracle()))
     return _lib
+
+
+def set_threads(n):
+    """Threads the oracle's time step may use in this process (OpenMP over
+    the cells; the same results bit for bit on any count). n <= 0 keeps the
+    setting. Returns the count in effect."""
+    return int(load().vlbo_set_threads(int(n)))
 
 
 def load_library(path):
