@@ -524,7 +524,9 @@ def storage16_leg(a, gmesh, prm, rho, u, stream, storage="f16"):
             "unit": "MLUPS", "ms_per_step": ms / a.steps, "steps": a.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_cell_update": bpc,
-                         "kernel": "k_step<19,%s,float>" % ("__half" if storage == "f16" else "__nv_bfloat16")}}
+                         "traffic": ncu_traffic(ncell, "step_d3q19_f16_channel_ncu.md") if storage == "f16" else None,
+                         "kernel": "k_step<19,%s,float>" % ("__half" if storage == "f16" else "__nv_bfloat16"),
+                         "source_sha": source_sha()}}
 
 
 PRECISION_FORMS = [("f64", "uniform"), ("f32", "uniform"), ("f16", "rest"), ("f16", "uniform"),
