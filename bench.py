@@ -22,6 +22,8 @@ update) reaches.
                   [--workload precision --n 384 --drift-steps 10000]   (FP32 / FP16 / BF16
                       storage: MLUPS at N^3, error against the FP64 GPU path and the
                       oracle on a 64^3 instance, total-mass drift)
+                  [--workload nn-forward]   (warm-start network forward pass, tensor cores
+                      against CUDA cores)
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas of the workload,
 no collective on the data path (weak scaling); timing is the max over ranks.
@@ -82,7 +84,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="channel",
-                    choices=["channel", "batch", "warmstart", "d3q39", "precision"],
+                    choices=["channel", "batch", "warmstart", "d3q39", "precision", "nn-forward"],
                     help="batch: many uneven D2Q9 meshes advanced by one launch per step; "
                          "warmstart: train the warm-start network and compare time to steady")
     ap.add_argument("--ntrain", type=int, default=2048)
@@ -647,6 +649,44 @@ def bench_precision(a):
     print(json.dumps(line))
 
 
+def bench_nn_forward(a):
+    """Forward passes of the warm-start network (width 64, 8 input channels,
+    32 x 64 grid, batch 32, bfloat16 storage): the 3x3 layers on the tensor
+    cores (tcgen05) against every layer on the CUDA cores."""
+    import torch
+
+    from paper_2401_17183_gb300 import build as B
+    B.build()
+    from paper_2401_17183_gb300 import nn
+    nn.load()
+    H, W, bt, wd = 32, 64, 32, 64
+    net = nn.Net(8, 3, wd, H, W, bt, storage=nn.VLB_NN_BF16, seed=7)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.rand((bt, 8, H, W), device="cuda", generator=g) * 2 - 1
+    y = torch.zeros((bt, 3, H, W), device="cuda")
+    res = {}
+    for tc in (True, False):
+        net.set_tensor_cores(tc)
+        for _ in range(a.warmup):
+            net.forward(x.data_ptr(), y.data_ptr(), bt)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            net.forward(x.data_ptr(), y.data_ptr(), bt)
+        e1.record()
+        torch.cuda.synchronize()
+        res["tensor_cores" if tc else "cuda_cores"] = e0.elapsed_time(e1) / a.steps
+    line = {"metric": "warm-start network forward pass, ms per batch", "value": res["tensor_cores"], "unit": "ms",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 storage, f32 accumulation", "data": "synthetic (uniform inputs)",
+            "config": {"workload": "unet_w64_8ch_32x64_batch32_bf16"},
+            "cuda_cores_ms": res["cuda_cores"], "speedup": res["cuda_cores"] / res["tensor_cores"],
+            "gpu_launches": None}
+    print(json.dumps(line))
+
+
 def warmstart_leg(ntrain, ntest, iters):
     """Steps and wall time to a 1e-6 residual from the learned prediction and
     from rest, on held-out members of the bumped 2D channel family."""
@@ -711,6 +751,8 @@ def main():
         return bench_d3q39(a)
     if a.workload == "precision":
         return bench_precision(a)
+    if a.workload == "nn-forward":
+        return bench_nn_forward(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -45,8 +45,16 @@ int vlb_nn_num_params(const vlb_nn *net, int64_t *n);
 int vlb_nn_get_params(const vlb_nn *net, float *host);
 int vlb_nn_set_params(vlb_nn *net, const float *host);
 /* y = net(x); x [B][Ci][H][W], y [B][Co][H][W] device FP32, B <= max_batch.
- * Keeps what the backward pass needs. */
+ * Keeps what the backward pass needs. With bfloat16 storage, a 3x3 layer
+ * whose Co is a power of two in [16, 256], whose grid has a multiple of 128
+ * cells and whose Ci is a multiple of 8 runs on the tensor cores (tcgen05:
+ * an implicit GEMM with FP32 accumulators in tensor memory); the others,
+ * the FP32 storage and the backward pass run on the CUDA cores. VLB_ECUDA if
+ * a tensor-core layer gave up waiting (one second) for its MMAs. */
 int vlb_nn_forward(vlb_nn *net, const float *d_x, float *d_y, int32_t batch);
+/* Whether bfloat16 forward passes may use the tensor cores (default 1); 0
+ * runs every layer on the CUDA cores (for comparison). */
+int vlb_nn_set_tensor_cores(vlb_nn *net, int32_t enable);
 /* Mean-square loss over all outputs against d_target and its gradient with
  * respect to y, written to d_dy (may alias nothing else); loss is returned in
  * host *loss. */

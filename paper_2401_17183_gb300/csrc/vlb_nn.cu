@@ -18,6 +18,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/vlb.h"
@@ -112,6 +113,196 @@ __global__ void __launch_bounds__(kThreads) k_conv(const TI *__restrict__ in, in
     if (RELU) v = fmaxf(v, 0.0f);
     ob[(int64_t)(co0 + o) * HW] = st<TO>(v);
   }
+}
+
+// ------------------------------------------------- tensor-core convolution
+// The 3x3 forward convolution of bfloat16 activations and weights as an
+// implicit GEMM on the fifth-generation tensor cores (tcgen05, sm_100 and
+// later): for the 128 output pixels p of a tile and kk = ci * 9 + tap,
+//   D[p][co] = sum_kk A[p][kk] B[co][kk],  A = the input patches (gathered
+//   on the fly), B = w[co][ci][tap] (K-contiguous as stored),
+// one MMA of M = 128, N = Co, K = 16 per step, FP32 accumulators in tensor
+// memory. The operands go through two shared-memory stages in the
+// no-swizzle K-major layout of 8-row x 16-byte core matrices (core (r/8,
+// k/8) at (r/8) * 256 + (k/8) * 128 bytes), each stage guarded by an mbarrier
+// that the MMA's commit arrives on. Every wait is bounded in time; a block
+// that gives up sets *err, waits (bounded) for its own MMAs and frees its
+// tensor memory.
+constexpr int kTcM = 128;   // output pixels per tile (MMA M)
+constexpr uint64_t kTcWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// shared-memory matrix descriptor: start address, leading (K-direction)
+// byte offset 128 and stride (M/N-direction) byte offset 256, all >> 4; the
+// descriptor version bit (46); no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ int core_off(int r, int k) {
+  return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// wait until the mbarrier has completed the phase of the given parity, at
+// most until t0 + kTcWaitNs; returns whether it did
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t t0) {
+  uint32_t done = 0;
+  while (true) {
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > kTcWaitNs) return false;
+  }
+}
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// out[b][co][p] = act(bias[co] + sum_ci sum_tap w[co][ci][tap] in[b][ci][p + off_tap])
+// for Co = N output channels; grid (H * W / 128, B), block 128 (thread t
+// gathers the patch of pixel p0 + t and, in the epilogue, reads TMEM lane t).
+// Needs H * W a multiple of 128, Ci a multiple of 8 (16-byte weight pieces)
+// and 16-byte aligned weights.
+template <int N, bool RELU>
+__global__ void __launch_bounds__(kTcM) k_conv3_tc(const __nv_bfloat16 *__restrict__ in, int64_t ibs,
+                                                  const __nv_bfloat16 *__restrict__ w, const float *__restrict__ bias,
+                                                  __nv_bfloat16 *__restrict__ out, int64_t obs, int Ci, int H, int W,
+                                                  int *err) {
+  static_assert(N % 16 == 0 && N >= 16 && N <= 256, "MMA N for M = 128");
+  constexpr int TCOLS = N < 32 ? 32 : N;   // tensor-memory columns: a power of two, at least 32
+  static_assert((TCOLS & (TCOLS - 1)) == 0, "N must be a power of two");
+  __shared__ __align__(1024) unsigned char sA[2][kTcM * 32];
+  __shared__ __align__(1024) unsigned char sB[2][N * 32];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int HW = H * W, p = blockIdx.x * kTcM + tid, b = blockIdx.y;
+  const int y = p / W, x = p - y * W;
+  const int K9 = Ci * 9, nch = (K9 + 15) / 16;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tslot;
+  // instruction descriptor: FP32 accumulators, bfloat16 A and B, both
+  // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+  const __nv_bfloat16 *inb = in + (int64_t)b * ibs;
+  // the operands of step j in registers: this pixel's 16 patch values as
+  // bfloat16 pairs, and this thread's 16-byte weight pieces; they are loaded
+  // one step ahead, so that their latency overlaps the previous MMA
+  constexpr int NQ = (2 * N + kTcM - 1) / kTcM;   // weight pieces per thread
+  uint32_t pa[8];
+  uint4 pb[NQ];
+  auto load_step = [&](int j) {
+#pragma unroll
+    for (int e = 0; e < 16; e += 2) {
+      __nv_bfloat16 v2[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int kk = j * 16 + e + u;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+        if (kk < K9) {
+          const int ci = kk / 9, tap = kk - ci * 9;
+          const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+          if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = inb[(int64_t)ci * HW + yy * W + xx];
+        }
+        v2[u] = v;
+      }
+      pa[e / 2] = pack_bf16(v2[0], v2[1]);
+    }
+    // (a piece lies wholly inside or wholly past the row end: 9 Ci is a
+    // multiple of 8)
+#pragma unroll
+    for (int i = 0; i < NQ; i++) {
+      const int q = tid + i * kTcM, kk0 = j * 16 + (q & 1) * 8;
+      pb[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (q < 2 * N && kk0 < K9) pb[i] = *reinterpret_cast<const uint4 *>(w + (int64_t)(q >> 1) * K9 + kk0);
+    }
+  };
+  const uint64_t t0 = gtimer();
+  bool ok = true;
+  int issued = 0;
+  load_step(0);
+  for (int j = 0; j < nch; j++) {
+    const int s = j & 1;
+    // the MMA of step j - 2 read this stage
+    bool late = false;
+    if (j >= 2) late = !mbar_wait(smem_u32(&bar[s]), ((j - 2) >> 1) & 1, t0);
+    if (__syncthreads_or(late)) {
+      ok = false;
+      break;
+    }
+    // A: two 16-byte pieces of this pixel's row; B: this thread's weight pieces
+    *reinterpret_cast<uint4 *>(&sA[s][core_off(tid, 0)]) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
+    *reinterpret_cast<uint4 *>(&sA[s][core_off(tid, 8)]) = make_uint4(pa[4], pa[5], pa[6], pa[7]);
+#pragma unroll
+    for (int i = 0; i < NQ; i++) {
+      const int q = tid + i * kTcM;
+      if (q < 2 * N) *reinterpret_cast<uint4 *>(&sB[s][core_off(q >> 1, (q & 1) * 8)]) = pb[i];
+    }
+    // the stores above are read by the tensor cores (the async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(umma_desc(smem_u32(&sA[s][0]))), "l"(umma_desc(smem_u32(&sB[s][0]))), "r"(idesc), "r"(j > 0 ? 1 : 0));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar[s]))
+                   : "memory");
+    }
+    issued = j + 1;
+    if (j + 1 < nch) load_step(j + 1);
+  }
+  // the last MMA done (its commit also covers every earlier one)
+  bool late = false;
+  if (issued > 0) late = !mbar_wait(smem_u32(&bar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1, gtimer());
+  if (__syncthreads_or(late)) ok = false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && issued == nch) {
+    // epilogue: warp w reads TMEM lanes 32w.. (pixels), 16 channels at a time
+    __nv_bfloat16 *ob = out + (int64_t)b * obs + p;
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int u = 0; u < 16; u++) {
+        float v = __uint_as_float(r[u]) + (bias ? bias[c0 + u] : 0.0f);
+        if (RELU) v = fmaxf(v, 0.0f);
+        ob[(int64_t)(c0 + u) * HW] = __float2bfloat16_rn(v);
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // wt[ci][co][k'] = w[co][ci][K*K - 1 - k'] (FP32): the weights of the
@@ -357,6 +548,8 @@ struct vlb_nn {
   double *lossp = nullptr;
   int64_t act_n = 0, wt_n = 0, dwp_n = 0;
   int nsplit = 16;
+  int *d_err = nullptr;      // set by a tensor-core convolution that gave up waiting
+  int tc = 1;                // 3x3 forward convolutions in bfloat16 on the tensor cores where they fit
   // activation views (offsets in act / gr), per sample sizes
   View x_in, e1, c1, s1, p1, e2, c2, s2, p2, e3, b3, d2, t2, d1, t1;
 };
@@ -371,9 +564,44 @@ namespace {
                             cudaGetErrorString(e_));                                              \
   } while (0)
 
+// the tensor-core form of a 3x3 layer (bfloat16 storage): Co a power of two
+// in [16, 256], H * W a multiple of 128, Ci a multiple of 8 and the layer's
+// weights 16-byte aligned
+inline bool tc_fits(const vlb_nn *n, const NNLayer &l) {
+  const bool pow2 = l.cout >= 16 && l.cout <= 256 && (l.cout & (l.cout - 1)) == 0;
+  // (16-byte weight pieces: the layer's weights start on a multiple of 8 elements)
+  return n->tc && n->storage == VLB_NN_BF16 && l.k == 3 && pow2 && ((int64_t)l.h * l.w) % nn::kTcM == 0 &&
+         l.cin % 8 == 0 && l.woff % 8 == 0;
+}
+
+template <int N>
+void launch_tc(const vlb_nn *n, const NNLayer &l, const __nv_bfloat16 *in, int64_t ibs, const __nv_bfloat16 *w,
+               const float *bias, __nv_bfloat16 *out, int64_t obs, bool relu, int B) {
+  const dim3 grid((unsigned)((int64_t)l.h * l.w / nn::kTcM), (unsigned)B);
+  if (relu)
+    nn::k_conv3_tc<N, true><<<grid, nn::kTcM>>>(in, ibs, w, bias, out, obs, l.cin, l.h, l.w, n->d_err);
+  else
+    nn::k_conv3_tc<N, false><<<grid, nn::kTcM>>>(in, ibs, w, bias, out, obs, l.cin, l.h, l.w, n->d_err);
+}
+
 template <typename T>
 int conv(const vlb_nn *n, const NNLayer &l, const T *in, int64_t ibs, const void *w, const float *bias, void *out,
          int64_t obs, bool relu, bool out_f32, int B) {
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    if (tc_fits(n, l)) {
+      const __nv_bfloat16 *wb = static_cast<const __nv_bfloat16 *>(w);
+      __nv_bfloat16 *ob = static_cast<__nv_bfloat16 *>(out);
+      switch (l.cout) {
+        case 16: launch_tc<16>(n, l, in, ibs, wb, bias, ob, obs, relu, B); break;
+        case 32: launch_tc<32>(n, l, in, ibs, wb, bias, ob, obs, relu, B); break;
+        case 64: launch_tc<64>(n, l, in, ibs, wb, bias, ob, obs, relu, B); break;
+        case 128: launch_tc<128>(n, l, in, ibs, wb, bias, ob, obs, relu, B); break;
+        default: launch_tc<256>(n, l, in, ibs, wb, bias, ob, obs, relu, B); break;
+      }
+      NN_CU(cudaGetLastError());
+      return VLB_OK;
+    }
+  }
   const dim3 grid((unsigned)(((l.w + nn::kTile - 1) / nn::kTile) * ((l.h + nn::kTile - 1) / nn::kTile)),
                   (unsigned)((l.cout + nn::kCo - 1) / nn::kCo), (unsigned)B);
   const bool bf = n->storage == VLB_NN_BF16;
@@ -500,6 +728,12 @@ int forward_t(vlb_nn *n, const float *d_x, float *d_y, int B) {
   NN_TRY(conv<T>(n, L[10], A + n->t1.off, n->t1.bs, wp(L[10]), n->p + L[10].boff, d_y, (int64_t)n->co * H * W, false,
                  true, B));
   NN_CU(cudaDeviceSynchronize());
+  int err = 0;
+  NN_CU(cudaMemcpy(&err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    cudaMemset(n->d_err, 0, sizeof(int));
+    return vlb::set_error(VLB_ECUDA, "vlb_nn_forward: a tensor-core convolution gave up waiting for its MMAs");
+  }
   return VLB_OK;
 }
 
@@ -659,6 +893,8 @@ int vlb_nn_create(int32_t in_ch, int32_t out_ch, int32_t width, int32_t H, int32
   if (e == cudaSuccess) e = cudaMalloc(&n->wt, sizeof(float) * n->wt_n);
   if (e == cudaSuccess) e = cudaMalloc(&n->dwp, sizeof(float) * n->dwp_n);
   if (e == cudaSuccess) e = cudaMalloc(&n->lossp, sizeof(double) * 1024);
+  if (e == cudaSuccess) e = cudaMalloc(&n->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(n->g, 0, sizeof(float) * n->np);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, sizeof(float) * n->np);
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, sizeof(float) * n->np);
@@ -703,6 +939,12 @@ int vlb_nn_set_params(vlb_nn *n, const float *host) {
   NN_CU(cudaMemcpy(n->p, host, sizeof(float) * n->np, cudaMemcpyHostToDevice));
   NN_TRY(refresh_compute_copy(n));
   NN_CU(cudaDeviceSynchronize());
+  return VLB_OK;
+}
+
+int vlb_nn_set_tensor_cores(vlb_nn *n, int32_t enable) {
+  if (!n) return vlb::set_error(VLB_EINVAL, "vlb_nn_set_tensor_cores: NULL net");
+  n->tc = enable ? 1 : 0;
   return VLB_OK;
 }
 
@@ -763,6 +1005,7 @@ void vlb_nn_destroy(vlb_nn *n) {
   cudaFree(n->wt);
   cudaFree(n->dwp);
   cudaFree(n->lossp);
+  if (n->d_err) cudaFree(n->d_err);
   delete n;
 }
 

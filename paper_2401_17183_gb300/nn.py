@@ -26,6 +26,7 @@ def load():
             "vlb_nn_get_params": ([vp, vp], C.c_int),
             "vlb_nn_set_params": ([vp, vp], C.c_int),
             "vlb_nn_forward": ([vp, vp, vp, C.c_int32], C.c_int),
+            "vlb_nn_set_tensor_cores": ([vp, C.c_int32], C.c_int),
             "vlb_nn_mse": ([vp, vp, vp, vp, C.c_int32, C.POINTER(C.c_double)], C.c_int),
             "vlb_nn_backward": ([vp, vp, C.c_int32], C.c_int),
             "vlb_nn_get_grads": ([vp, vp], C.c_int),
@@ -72,6 +73,9 @@ class Net:
         g = np.zeros(self.nparams, dtype=np.float32)
         _check(load().vlb_nn_get_grads(self.h, g.ctypes.data), "vlb_nn_get_grads")
         return g
+
+    def set_tensor_cores(self, enable):
+        _check(load().vlb_nn_set_tensor_cores(self.h, 1 if enable else 0), "vlb_nn_set_tensor_cores")
 
     def forward(self, d_x, d_y, batch):
         _check(load().vlb_nn_forward(self.h, d_x, d_y, batch), "vlb_nn_forward")

@@ -80,6 +80,29 @@ def test_bf16_storage_forward(NN):
     assert err < 3e-2, err
 
 
+def test_bf16_forward_on_tensor_cores(NN):
+    """Width 16 on a 32 x 64 grid: every 3x3 layer fits the tensor-core form
+    (tcgen05, FP32 accumulators in tensor memory). The forward pass matches
+    the FP64 reference as the CUDA-core form does, and the two forms agree
+    with each other to the rounding of the bfloat16 activations."""
+    torch, net, p, x, t, dx, dt, dy, ddy = _setup(NN, NN.VLB_NN_BF16, width=16, H=32, W=64, ci=8, co=3, B=2)
+    B = x.shape[0]
+    net.forward(dx.data_ptr(), dy.data_ptr(), B)
+    torch.cuda.synchronize()
+    y_tc = dy.cpu().numpy().copy()
+    net.set_tensor_cores(False)
+    net.forward(dx.data_ptr(), dy.data_ptr(), B)
+    torch.cuda.synchronize()
+    y_fma = dy.cpu().numpy().copy()
+    net.set_tensor_cores(True)
+    layers = ref.unpack(p, NN.layer_shapes(8, 3, 16))
+    yr = ref.forward(torch.from_numpy(x.astype(np.float64)), layers).detach().numpy()
+    nr = np.linalg.norm(yr)
+    assert np.linalg.norm(y_tc - yr) / nr < 3e-2
+    assert np.linalg.norm(y_fma - yr) / nr < 3e-2
+    assert np.linalg.norm(y_tc - y_fma) / nr < 1e-2
+
+
 def test_adam_step(NN):
     torch, net, p, x, t, dx, dt, dy, ddy = _setup(NN, NN.VLB_NN_F32)
     B = x.shape[0]
