@@ -1,6 +1,8 @@
 // vlb_geometry.cu -- FP64 geometry precompute of section 2.1 (done once per
 // mesh), mesh diagnostics, the coefficient records the step kernel streams,
 // and the equilibrium initialisation of the populations.
+#include <type_traits>
+
 #include "vlb_addr.cuh"
 #include "vlb_collide.cuh"
 #include "vlb_q39.cuh"
@@ -505,6 +507,64 @@ __global__ void k_init(const double *J, const double *gu, const double *ginv, co
   }
 }
 
+// The same initial state for FP32 arithmetic (FP32 or 16-bit storage relative
+// to the uniform reference n_ref): with J f^eq_a = J rho w_a (1 + x_a),
+//   N_a - w_a n_ref = w_a [(J rho - n_ref) + J rho x_a],
+// J rho - n_ref is formed in FP64 (one difference of large terms) and the
+// bracket x_a in FP32, so every FP32 term is of the size of the deviation.
+// (GB300's FP64 rate is a small fraction of its FP32 rate; the FP64 form of
+// k_init is bound by it.)
+template <int Q>
+__device__ __forceinline__ float eq_even_x(const EqParts<Q, float> &e, int a) {
+  constexpr int D = Lat<Q>::D;
+  float cbc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    const int ci = Lat<Q>::c(a, i);
+    if (ci == 0) continue;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      const int cj = Lat<Q>::c(a, j);
+      if (cj == 0) continue;
+      if (ci * cj > 0)
+        cbc += e.B[i][j];
+      else
+        cbc -= e.B[i][j];
+    }
+  }
+  return (3.0f * cbc - e.trB) * 1.5f;
+}
+
+template <int Q, typename S>
+__global__ void k_init_f32(const double *J, const double *gu, const double *ginv, const double *rho,
+                           const double *u, int64_t ncell, double nref, S *f) {
+  constexpr int D = Lat<Q>::D, NS = D * (D + 1) / 2, H = Lat<Q>::H;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  float U[D], gd[NS], zero[D];
+  for (int i = 0; i < D; i++) {
+    float s = 0.0f;
+    for (int d = 0; d < D; d++) s = fmaf((float)u[c * D + d], (float)gu[(c * D + i) * D + d], s);
+    U[i] = s;
+    zero[i] = 0.0f;
+  }
+  // g^ii - 1 formed in FP64 before rounding
+  for (int i = 0; i < D; i++)
+    for (int j = i; j < D; j++)
+      gd[sym<D>(i, j)] = (float)(ginv[c * NS + sym<D>(i, j)] - (i == j ? 1.0 : 0.0));
+  EqParts<Q, float> e;
+  eq_parts<Q, float>(gd, U, zero, e);
+  const double jr = J[c] * rho[c];
+  const float md = (float)(jr - nref), jrf = (float)jr;
+  f[c] = store_s<S>(lat_w<Q, float>(0) * fmaf(jrf, eq_even_x<Q>(e, 0), md));
+#pragma unroll
+  for (int p = 1; p <= H; p++) {
+    const float xe = eq_even_x<Q>(e, p), xo = eq_odd<Q, float>(e, U, p), w = lat_w<Q, float>(p);
+    f[p * ncell + c] = store_s<S>(w * fmaf(jrf, xe + xo, md));
+    f[(p + H) * ncell + c] = store_s<S>(w * fmaf(jrf, xe - xo, md));
+  }
+}
+
 cudaError_t launch_init(const vlb_sim *sim, const double *d_rho, const double *d_u, cudaStream_t s) {
   const vlb_mesh *m = sim->mesh;
   const int threads = 128;
@@ -512,6 +572,19 @@ cudaError_t launch_init(const vlb_sim *sim, const double *d_rho, const double *d
   const RefCtx ref = make_ref(sim);
   return with_storage(sim->p.precision, [&](auto tag) {
     using S = typename decltype(tag)::type;
+    if constexpr (!std::is_same<S, double>::value) {
+      // FP32 arithmetic for the uniform reference (the rest reference of
+      // 16-bit storage keeps the FP64 form)
+      if (!ref.rest) {
+        if (m->md.q == 9)
+          k_init_f32<9, S><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u, m->ncell,
+                                                                ref.nref, (S *)sim->d_f);
+        else
+          k_init_f32<19, S><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u, m->ncell,
+                                                                 ref.nref, (S *)sim->d_f);
+        return cudaGetLastError();
+      }
+    }
     if (m->md.q == 9)
       k_init<9, S><<<(unsigned)blocks, threads, 0, s>>>(m->d_J, m->d_gu, m->d_ginv, d_rho, d_u, m->ncell,
                                                         ref, (S *)sim->d_f);
