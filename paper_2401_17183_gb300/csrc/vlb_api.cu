@@ -340,7 +340,11 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
   s->nc = q == 9    ? (plane ? L9::stride<float, true>() : L9::stride<float, false>())
           : q == 19 ? (plane ? L19::stride<float, true>() : L19::stride<float, false>())
                     : 0;  // D3Q39: no records, the kernels read the mesh geometry
-  if (q == VLB_D3Q39) s->ncoef = 0;
+  if (q == VLB_D3Q39) {
+    // D3Q39: no records; per cell the chord data of its force map (q39_prepare)
+    s->nc = 12;
+    s->ncoef = mesh->ncell;
+  }
   const size_t es = f64 ? 8 : 4;
   // 16 bytes of padding: a 16-bit population is read as the aligned 32-bit
   // word that contains it
@@ -351,7 +355,7 @@ int vlb_init(const vlb_mesh *mesh, const vlb_params *params, const double *rho, 
     vlb_destroy(s);
     return fail(VLB_ENOMEM, "simulation device allocation: %s", cudaGetErrorString(e));
   }
-  e = q == VLB_D3Q39 ? cudaSuccess : vlb::launch_pack_coef(s, s->stream);
+  e = q == VLB_D3Q39 ? vlb::q39_prepare(s, s->stream) : vlb::launch_pack_coef(s, s->stream);
   if (e != cudaSuccess) {
     vlb_destroy(s);
     return fail(VLB_ECUDA, "coefficient pack: %s", cudaGetErrorString(e));

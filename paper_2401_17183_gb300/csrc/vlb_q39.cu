@@ -44,6 +44,10 @@ struct Q39Args {
   int64_t ncell;
   int64_t n[3];
   const double *J, *gl, *gu, *ginv, *K;
+  // per cell: the chord matrix H = (I - dG/dF)^-1 of the force map at the
+  // rest state (row-major) and the rest state's force at rho = 1, 12 values;
+  // NULL before q39_prepare has filled them
+  const double *chord;
   double body[3];
   double tau, tol;
   int32_t max_iter;
@@ -176,28 +180,44 @@ __device__ void eval39(const double N[kQ39], double J, double rho, const double 
   }
 }
 
-// The local fixed point on F from F = 0: converged when the change is at most
+// The local fixed point on F (Eq. 27 with the body force). With the cell's
+// chord data ch: the chord iteration F <- F + H (G(F) - F) from rho F_rest
+// (the map is homogeneous of degree one in (N, F) at rest, so rho F_rest is
+// the rest state's fixed point at density rho); H inverts the linear part of
+// G at rest, so a few evaluations suffice. Without it (ch NULL): the plain
+// iteration F <- G(F) from F = 0. Converged when the change is at most
 // tol max(rho, |F|); N' at the converged F. False if max_iter is reached.
 __device__ bool collide39(const double N[kQ39], double J, const double gd[3][3], const double G[3],
-                          const double *K, double tau, double tol, int max_iter, double Np[kQ39],
-                          double &rho, double U[3], double F[3]) {
+                          const double *K, const double *ch, double tau, double tol, int max_iter,
+                          double Np[kQ39], double &rho, double U[3], double F[3]) {
   rho = 0.0;
   for (int a = 0; a < kQ39; a++) rho += N[a] / J;
   for (int i = 0; i < 3; i++) {
     double s = 0.0;
     for (int a = 0; a < kQ39; a++) s += kT39.c[a][i] * (N[a] / J);
     U[i] = s / rho;
-    F[i] = 0.0;
+    F[i] = ch ? rho * ch[9 + i] : 0.0;
   }
   bool conv = false;
   double Fn[3];
   for (int it = 0; it < max_iter; it++) {
     eval39(N, J, rho, U, F, gd, G, K, tau, Np, Fn);
     double diff = 0.0, fmax = 0.0;
-    for (int i = 0; i < 3; i++) {
-      diff = maxnan(diff, fabs(Fn[i] - F[i]));
-      fmax = maxnan(fmax, fabs(Fn[i]));
-      F[i] = Fn[i];
+    if (ch) {
+      double r[3];
+      for (int i = 0; i < 3; i++) r[i] = Fn[i] - F[i];
+      for (int i = 0; i < 3; i++) {
+        const double d = ch[3 * i] * r[0] + ch[3 * i + 1] * r[1] + ch[3 * i + 2] * r[2];
+        F[i] += d;
+        diff = maxnan(diff, fabs(d));
+        fmax = maxnan(fmax, fabs(F[i]));
+      }
+    } else {
+      for (int i = 0; i < 3; i++) {
+        diff = maxnan(diff, fabs(Fn[i] - F[i]));
+        fmax = maxnan(fmax, fabs(Fn[i]));
+        F[i] = Fn[i];
+      }
     }
     if (diff <= tol * (rho > fmax ? rho : fmax)) {
       conv = true;
@@ -206,6 +226,55 @@ __device__ bool collide39(const double N[kQ39], double J, const double gd[3][3],
   }
   eval39(N, J, rho, U, F, gd, G, K, tau, Np, Fn);
   return conv;
+}
+
+// Chord data of every cell: the rest state N = J f^eq(1, 0) of Eq. 33, its
+// force F_rest by the plain iteration (to 1e-15), and the Jacobian of the map
+// F -> G(F) there by central differences (G is a cubic polynomial in F, so
+// the difference error is of the order of the step squared); H = (I - Jac)^-1.
+__global__ void __launch_bounds__(kQ39Threads) k_prep39(const Q39Args A, double *out) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double gd[3][3], G[3], U0[3] = {0.0, 0.0, 0.0}, N[kQ39], Np[kQ39], F[3] = {0.0, 0.0, 0.0}, Fn[3];
+    cell_metric(A, c, gd, G);
+    const double J = A.J[c];
+    feq39(1.0, U0, U0, gd, N);
+    for (int a = 0; a < kQ39; a++) N[a] *= J;
+    const double *K = A.K + c * kQ39 * 3;
+    for (int it = 0; it < 400; it++) {
+      eval39(N, J, 1.0, U0, F, gd, G, K, A.tau, Np, Fn);
+      double diff = 0.0, fm = 0.0;
+      for (int i = 0; i < 3; i++) {
+        diff = maxnan(diff, fabs(Fn[i] - F[i]));
+        fm = maxnan(fm, fabs(Fn[i]));
+        F[i] = Fn[i];
+      }
+      if (diff <= 1e-15 * (fm > 1.0 ? fm : 1.0)) break;
+    }
+    double Jac[3][3];
+    const double h = 1e-6;
+    for (int j = 0; j < 3; j++) {
+      double Fp[3] = {F[0], F[1], F[2]}, Fm[3] = {F[0], F[1], F[2]}, Gp[3], Gm[3];
+      Fp[j] += h;
+      Fm[j] -= h;
+      eval39(N, J, 1.0, U0, Fp, gd, G, K, A.tau, Np, Gp);
+      eval39(N, J, 1.0, U0, Fm, gd, G, K, A.tau, Np, Gm);
+      for (int i = 0; i < 3; i++) Jac[i][j] = (Gp[i] - Gm[i]) / (2.0 * h);
+    }
+    double M[3][3], C[3][3];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) M[i][j] = (i == j ? 1.0 : 0.0) - Jac[i][j];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        C[i][j] = M[i1][j1] * M[i2][j2] - M[i1][j2] * M[i2][j1];
+      }
+    const double det = M[0][0] * C[0][0] + M[0][1] * C[0][1] + M[0][2] * C[0][2];
+    double *o = out + c * 12;
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) o[3 * i + j] = C[j][i] / det;
+    for (int i = 0; i < 3; i++) o[9 + i] = F[i];
+  }
 }
 
 template <bool ODD>
@@ -219,7 +288,8 @@ __global__ void __launch_bounds__(kQ39Threads) k_step39(const Q39Args A) {
     for (int a = 0; a < kQ39; a++) N[a] = A.f[src39<ODD>(A, c, ic, a)];
     double gd[3][3], G[3], rho, U[3], F[3];
     cell_metric(A, c, gd, G);
-    if (!collide39(N, A.J[c], gd, G, A.K + c * kQ39 * 3, A.tau, A.tol, A.max_iter, Np, rho, U, F))
+    if (!collide39(N, A.J[c], gd, G, A.K + c * kQ39 * 3, A.chord ? A.chord + c * 12 : nullptr, A.tau, A.tol,
+                   A.max_iter, Np, rho, U, F))
       atomicOr(A.err, ERR_NOCONV);
 #pragma unroll 1
     for (int a = 0; a < kQ39; a++) A.f[dst39<ODD>(A, c, ic, a)] = Np[a];
@@ -262,7 +332,8 @@ __global__ void __launch_bounds__(kMomThreads) k_moments39(const Q39Args A, doub
     for (int a = 0; a < kQ39; a++) N[a] = A.f[src39<ODD>(A, c, ic, a)];
     double gd[3][3], G[3], rho, U[3], F[3];
     cell_metric(A, c, gd, G);
-    if (!collide39(N, A.J[c], gd, G, A.K + c * kQ39 * 3, A.tau, A.tol, A.max_iter, Np, rho, U, F))
+    if (!collide39(N, A.J[c], gd, G, A.K + c * kQ39 * 3, A.chord ? A.chord + c * 12 : nullptr, A.tau, A.tol,
+                   A.max_iter, Np, rho, U, F))
       atomicOr(A.err, ERR_NOCONV);
     const double *gl = A.gl + c * 9;
     out[c] = rho;
@@ -374,6 +445,7 @@ Q39Args make_args(const vlb_sim *sim) {
   A.gu = m->d_gu;
   A.ginv = m->d_ginv;
   A.K = m->d_K;
+  A.chord = static_cast<const double *>(sim->d_coef);
   A.tau = sim->p.tau;
   A.tol = sim->p.tol;
   A.max_iter = sim->p.max_iter;
@@ -394,6 +466,13 @@ unsigned grid_for(int64_t ncell, int threads) {
 
 cudaError_t q39_mesh_stats(const vlb_mesh *m, double *d_partial, int64_t nblk, cudaStream_t s) {
   k_stats39<<<(unsigned)nblk, kStatThreads, 0, s>>>(m->d_J, m->d_ginv, m->ncell, d_partial);
+  return cudaGetLastError();
+}
+
+cudaError_t q39_prepare(const vlb_sim *sim, cudaStream_t s) {
+  Q39Args A = make_args(sim);
+  A.chord = nullptr;
+  k_prep39<<<grid_for(A.ncell, kQ39Threads), kQ39Threads, 0, s>>>(A, static_cast<double *>(sim->d_coef));
   return cudaGetLastError();
 }
 

@@ -50,6 +50,8 @@ __host__ __device__ constexpr double q39_w(int a) {
 
 // launches of the D3Q39 path (FP64 populations, periodic meshes)
 cudaError_t q39_mesh_stats(const vlb_mesh *m, double *d_partial, int64_t nblk, cudaStream_t s);
+// per-cell chord data of the force map into sim->d_coef (12 doubles per cell)
+cudaError_t q39_prepare(const vlb_sim *sim, cudaStream_t s);
 cudaError_t q39_init(const vlb_sim *sim, const double *d_rho, const double *d_u, cudaStream_t s);
 cudaError_t q39_step(const vlb_sim *sim, int odd, cudaStream_t s);
 cudaError_t q39_moments(const vlb_sim *sim, double *d_out, double *d_partial, int64_t nblk, cudaStream_t s);
