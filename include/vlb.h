@@ -242,11 +242,11 @@ int vlb_batch_step(vlb_batch *b, int64_t nsteps);
 int vlb_batch_tune(vlb_batch *b, int32_t steps, int64_t *run_length_out);
 /* The number of steps vlb_batch_tune(b, steps, ...) advances every member by. */
 int vlb_batch_tune_steps(const vlb_batch *b, int32_t steps, int64_t *advanced);
-/* Use block shape `shape` (0 .. 3 for VLB_F32 members, 0 .. 1 for VLB_F64, in
- * the order 128 threads with the single-mesh step's register budget, 128
- * with a smaller one, then the same two budgets at 64 threads) with its
- * default run length, about two runs per resident block. EINVAL outside
- * that range. */
+/* Use block shape `shape` with its default run length, about two runs per
+ * resident block. VLB_F32 members: 0 .. 3 = 128 threads cut for 3, 6 or 8
+ * resident blocks per SM (the first is the single-mesh step's budget), then
+ * 64 threads cut for 12; VLB_F64 members: 0 .. 1 = 128 threads for 2 blocks,
+ * 64 threads for 4. EINVAL outside that range. */
 int vlb_batch_set_shape(vlb_batch *b, int32_t shape);
 /* The block shape in use: threads per block (= tile width) and the resident
  * blocks per SM its kernel's registers were cut for. Either may be NULL. */

@@ -32,7 +32,7 @@ struct BatchKind {
 struct BatchShape {
   int threads, min_blocks;
 };
-constexpr BatchShape kShapes32[] = {{128, 3}, {128, 6}, {64, 6}, {64, 12}};
+constexpr BatchShape kShapes32[] = {{128, 3}, {128, 6}, {128, 8}, {64, 12}};
 constexpr BatchShape kShapes64[] = {{128, 2}, {64, 4}};
 constexpr int kNShapes32 = sizeof(kShapes32) / sizeof(kShapes32[0]);
 constexpr int kNShapes64 = sizeof(kShapes64) / sizeof(kShapes64[0]);
