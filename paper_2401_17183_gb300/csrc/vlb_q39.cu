@@ -186,7 +186,8 @@ __device__ void eval39(const double N[kQ39], double J, double rho, const double 
 // the rest state's fixed point at density rho); H inverts the linear part of
 // G at rest, so a few evaluations suffice. Without it (ch NULL): the plain
 // iteration F <- G(F) from F = 0. Converged when the change is at most
-// tol max(rho, |F|); N' at the converged F. False if max_iter is reached.
+// tol max(rho, |F|); N' at the converged F (to within that change). False if
+// max_iter is reached.
 __device__ bool collide39(const double N[kQ39], double J, const double gd[3][3], const double G[3],
                           const double *K, const double *ch, double tau, double tol, int max_iter,
                           double Np[kQ39], double &rho, double U[3], double F[3]) {
@@ -224,7 +225,10 @@ __device__ bool collide39(const double N[kQ39], double J, const double gd[3][3],
       break;
     }
   }
-  eval39(N, J, rho, U, F, gd, G, K, tau, Np, Fn);
+  // N' at the converged F: with the chord iteration the last evaluation was
+  // at the F that the final correction, below tol max(rho, |F|), moved off,
+  // so its N' is kept; the plain iteration evaluates once more
+  if (!(ch && conv)) eval39(N, J, rho, U, F, gd, G, K, tau, Np, Fn);
   return conv;
 }
 
