@@ -64,6 +64,10 @@ struct StepArgs {
   int32_t ntf, nA, nB;
   int64_t per_block;  // tiles per block (contiguous runs)
   int32_t full_tiles; // the fastest axis is a whole number of tiles
+  // offsets of the population slots, k ncell and k ncell / 2 (32-bit words
+  // of 16-bit storage), when every offset fits in 32 bits (else unused):
+  // read by the kernel as constants, not formed per cell and direction
+  int32_t soff[19], soffw[19];
 };
 
 constexpr int kStepThreads = 128;
@@ -118,15 +122,6 @@ struct TileCursor {
 template <int Q, typename IT>
 __device__ __forceinline__ Addr<Q, IT> tile_addr(const Grid &g, const TileCursor &c, IT ifast) {
   return Lat<Q>::D == 3 ? Addr<Q, IT>(g, (IT)c.A, (IT)c.B, ifast) : Addr<Q, IT>(g, (IT)c.B, ifast, (IT)0);
-}
-
-// index of the arrived population N_a(q, t) (the A-A read side): slot a of q
-// (even parity, the rest population, or a link that comes back from a wall)
-// or slot abar of q - c_a
-template <int Q, bool ODD, typename IT>
-__device__ __forceinline__ IT src_index(IT ps, const Addr<Q, IT> &ad, int a) {
-  if (!ODD || a == 0 || ad.crosses(a, -1)) return (IT)a * ps + ad.cell;
-  return (IT)lat_opp<Q>(a) * ps + ad.nb(a, -1);
 }
 
 // does c_a move along a slow axis (and so, in plane mode, to another column)?
@@ -188,10 +183,17 @@ __device__ __forceinline__ __nv_bfloat16 s16_from_bits<__nv_bfloat16>(unsigned s
 // nfast - 1 is odd) the other one.
 // The tiles [t0, t1) of one mesh, as one block of T threads (tiles of T
 // cells; the arguments' tile counts must be those of width T).
+// TAB: the slot offsets come from the argument table (the arguments are
+// kernel parameters, so each offset is a constant operand) rather than from a
+// product per cell and direction; only with 32-bit offsets.
+// Cells away from every wall (on odd steps) index their neighbours with no
+// wall test and no select: every move is a plain or a periodic one.
 template <int Q, typename S, typename R, bool ODD, bool PLANE, bool REFOFS, bool HPAR, typename IT,
-          int T = kStepThreads>
+          int T = kStepThreads, bool TAB = true>
 __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, const int64_t t1) {
   constexpr int D = Lat<Q>::D, H = Lat<Q>::H;
+  static_assert(Q <= 19, "the slot-offset table holds 19 directions");
+  constexpr bool USE_TAB = TAB && sizeof(IT) == 4;
   using L = CoefLayout<Q>;
   constexpr int RS = L::template stride<R, PLANE>();
   constexpr bool H16 = sizeof(S) == 2;
@@ -209,6 +211,32 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
 
   // pieces of 16 bytes in one direction's row segment of a tile
   constexpr int PER_ROW = T * (int)sizeof(S) / 16;
+
+  // offset of slot k in elements (soff) and in 32-bit words of 16-bit
+  // storage (soffw)
+  auto soff = [&](int k) -> IT {
+    if constexpr (USE_TAB)
+      return (IT)a.soff[k];
+    else
+      return (IT)k * ps;
+  };
+  auto soffw = [&](int k) -> IT {
+    if constexpr (USE_TAB)
+      return (IT)a.soffw[k];
+    else
+      return (IT)k * (ps / 2);
+  };
+  // index of the arrived population N_a(q, t) (the A-A read side): slot a of
+  // q (even parity, the rest population, or a link that comes back from a
+  // wall) or slot abar of q - c_a; WALLS false: q is known to be away from
+  // every wall. ws: the slot offsets to use (elements or words).
+  auto src_idx = [&](const Addr<Q, IT> &ad, int av, auto walls_tag, auto ws) -> IT {
+    constexpr bool WALLS = decltype(walls_tag)::value;
+    if (!ODD || av == 0 || (WALLS && ad.crosses(av, -1))) return ws(av) + ad.cell;
+    return ws(lat_opp<Q>(av)) + ad.nb(av, -1);
+  };
+  const std::true_type walls_yes;
+  const std::false_type walls_no;
 
   // issue this thread's copies for tile c into stage st: the populations of
   // its cell and, in plane mode, one 16-byte piece of the shared record. On
@@ -244,23 +272,31 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
         }
         adw.dp[D - 1] = ((ad.cell + ad.dp[D - 1]) >> 1) - adw.cell;
         adw.dm[D - 1] = ((ad.cell + ad.dm[D - 1]) >> 1) - adw.cell;
+        const uint32_t *fw = reinterpret_cast<const uint32_t *>(f);
+        if (ODD && !ad.wall_cell()) {
 #pragma unroll
-        for (int av = 0; av < Q; av++)
-          cp_async<4>(&sm.pop[st][av][tid],
-                      reinterpret_cast<const uint32_t *>(f) + src_index<Q, ODD, IT>(ps / 2, adw, av));
+          for (int av = 0; av < Q; av++) cp_async<4>(&sm.pop[st][av][tid], fw + src_idx(adw, av, walls_no, soffw));
+        } else {
+#pragma unroll
+          for (int av = 0; av < Q; av++) cp_async<4>(&sm.pop[st][av][tid], fw + src_idx(adw, av, walls_yes, soffw));
+        }
       } else if constexpr (H16) {
         uint32_t hi = 0;
 #pragma unroll
         for (int av = 0; av < Q; av++) {
-          const IT idx = src_index<Q, ODD, IT>(ps, ad, av);
+          const IT idx = src_idx(ad, av, walls_yes, soff);
           cp_async<4>(&sm.pop[st][av][tid], reinterpret_cast<const uint32_t *>(f) + (idx >> 1));
           hi |= (uint32_t)(idx & 1) << av;
         }
         sm.half_hi[st][tid] = hi;
       } else {
+        if (ODD && !ad.wall_cell()) {
 #pragma unroll
-        for (int av = 0; av < Q; av++)
-          cp_async<sizeof(S)>(&sm.pop[st][av][tid], f + src_index<Q, ODD, IT>(ps, ad, av));
+          for (int av = 0; av < Q; av++) cp_async<sizeof(S)>(&sm.pop[st][av][tid], f + src_idx(ad, av, walls_no, soff));
+        } else {
+#pragma unroll
+          for (int av = 0; av < Q; av++) cp_async<sizeof(S)>(&sm.pop[st][av][tid], f + src_idx(ad, av, walls_yes, soff));
+        }
       }
     }
     if constexpr (PLANE) {
@@ -396,23 +432,36 @@ __device__ __forceinline__ void step_tiles(const StepArgs &a, const int64_t t0, 
         }
       }
 
-      // ---- push (write side of Eq. 22)
+      // ---- push (write side of Eq. 22): own slot abar (even steps, and a
+      //      link through a wall), else slot a of q + c_a; WALLS false: the
+      //      cell is away from every wall
+      auto push = [&](auto walls_tag) {
+        constexpr bool WALLS = decltype(walls_tag)::value;
 #pragma unroll
-      for (int av = 1; av < Q; av++) {
-        const int ab = lat_opp<Q>(av);
-        const bool crs = ad.crosses(av, 1);
-        R v = Np[av];
-        if constexpr (REFOFS && ODD) {
-          if (slow_move<Q>(av)) {
-            const int cz = Lat<Q>::c(av, D - 1);
-            const R dv = rc[L::DOUT + av];
-            v = cz == 0 ? v + dv : fmar(dv, cz > 0 ? (ad.hi[D - 1] ? R(0) : R(1)) : (ad.lo[D - 1] ? R(0) : R(1)), v);
+        for (int av = 1; av < Q; av++) {
+          const int ab = lat_opp<Q>(av);
+          const bool crs = WALLS && ad.crosses(av, 1);
+          R v = Np[av];
+          if constexpr (REFOFS && ODD) {
+            if (slow_move<Q>(av)) {
+              const int cz = Lat<Q>::c(av, D - 1);
+              const R dv = rc[L::DOUT + av];
+              if (WALLS)
+                v = cz == 0 ? v + dv
+                            : fmar(dv, cz > 0 ? (ad.hi[D - 1] ? R(0) : R(1)) : (ad.lo[D - 1] ? R(0) : R(1)), v);
+              else
+                v = v + dv;
+            }
           }
+          // one store through a selected index
+          const IT idx = (!ODD || crs) ? soff(ab) + cell : soff(av) + ad.nb(av, 1);
+          f[idx] = store_s<S>(v);
         }
-        // one store through a selected index (own slot abar, or slot a of q + c_a)
-        const IT idx = (!ODD || crs) ? (IT)ab * ps + cell : (IT)av * ps + ad.nb(av, 1);
-        f[idx] = store_s<S>(v);
-      }
+      };
+      if (ODD && !ad.wall_cell())
+        push(walls_no);
+      else
+        push(walls_yes);
       f[cell] = store_s<S>(Np[0]);
     }
     cur.next(a);
@@ -445,7 +494,8 @@ template <int Q, typename S, typename R, bool ODD, bool PLANE, typename IT, int 
 __global__ void __launch_bounds__(T, MINB)
     k_step_batch(const StepArgs *__restrict__ args, const BatchItem *__restrict__ items) {
   const BatchItem it = items[blockIdx.x];
-  step_tiles<Q, S, R, ODD, PLANE, false, false, IT, T>(args[it.sim], it.t0, it.t1);
+  // the arguments sit in global memory here: slot offsets are formed, not read
+  step_tiles<Q, S, R, ODD, PLANE, false, false, IT, T, false>(args[it.sim], it.t0, it.t1);
 }
 
 // Arguments of one simulation's step kernel for tiles of T cells (per_block
@@ -481,6 +531,11 @@ inline StepArgs make_step_args(const vlb_sim *sim, int T = kStepThreads) {
   a.ntiles = (int64_t)a.ntf * a.nA * a.nB;
   a.per_block = 0;
   a.full_tiles = nfast % T == 0 ? 1 : 0;
+  const bool i32 = (int64_t)Q * m->ncell < ((int64_t)1 << 31);
+  for (int k = 0; k < 19; k++) {
+    a.soff[k] = (i32 && k < Q) ? (int32_t)(k * m->ncell) : 0;
+    a.soffw[k] = (i32 && k < Q) ? (int32_t)(k * (m->ncell / 2)) : 0;
+  }
   return a;
 }
 
