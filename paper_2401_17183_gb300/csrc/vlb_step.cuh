@@ -133,13 +133,13 @@ __host__ __device__ constexpr bool slow_move(int a) {
 }
 
 // resident blocks per SM the register budget is cut for: 3 for FP32
-// arithmetic (168 registers, no spills; 4 blocks at 128 registers ran 0.5%
-// slower, 5 at 102 registers 18% slower), 4 for the even steps of 16-bit
-// storage (128 registers without spills, 3% faster than 3 blocks; their odd
-// steps took the same time at 4 blocks with 4% more instructions), 2 for FP64
+// storage (168 registers, no spills; 4 blocks at 128 registers ran 0.4%
+// slower, 5 at 102 registers 18% slower), 4 for 16-bit storage (128
+// registers; 3% faster than 3 blocks on even steps, 0.3% faster over both
+// parities), 2 for FP64
 template <typename R, typename S = R, bool ODD = false>
 constexpr int step_min_blocks() {
-  return sizeof(R) == 4 ? (sizeof(S) == 2 && !ODD ? 4 : 3) : 2;
+  return sizeof(R) == 4 ? (sizeof(S) == 2 ? 4 : 3) : 2;
 }
 
 // pipeline depth: tiles whose copies are in flight while one is collided
