@@ -2,7 +2,7 @@
 // 6th-order isotropic D3Q39 velocity set (vlb_q39.cuh) on periodic meshes, in
 // FP64. The reduced force map of the D3Q19/D2Q9 kernels relies on velocity
 // components in {-1, 0, 1}; here every relation of section 2.2 is evaluated
-// direction by direction instead:
+// pair of opposite directions by pair instead:
 //   f = N / J, rho and U (Eqs. 14, 15, 17); a fixed point on F (Eq. 27), each
 //   evaluation forming U~ = U + F / (2 rho), f^eq (Eq. 33 with T0 = 2/3),
 //   deltaPi (Eq. 30), deltaN (Eq. 31), Omega = -(N - J f^eq) / tau (Eq. 20)
@@ -98,60 +98,95 @@ __device__ void cell_metric(const Q39Args &A, int64_t c, double gd[3][3], double
   }
 }
 
-// Eq. 33 for every direction, with B^ij = (g^ij - delta^ij) T0 + U~^i U~^j and
-// C^ijk = T0 [(g^ij U~^k - delta^ij U^k) + cyclic] + U~^i U~^j U~^k:
-//   f^eq_a = rho w_a {1 + c.U / T0 + (c.B.c / T0 - tr B) / (2 T0)
-//                     + (C:ccc - 3 T0 c.V) / (6 T0^3)},  V^i = C^ijj
-__device__ void feq39(double rho, const double U[3], const double Ut[3], const double gd[3][3],
-                      double f[kQ39]) {
+// The two Hermite tensors of Eq. 33, with B^ij = (g^ij - delta^ij) T0 +
+// U~^i U~^j and C^ijk = T0 [(g^ij U~^k - delta^ij U^k) + cyclic] + U~^i U~^j U~^k,
+// V^i = C^ijj and tr B, formed once per evaluation
+struct Herm39 {
+  double B[3][3], C[3][3][3], V[3], trB;
+};
+__device__ void herm39(const double U[3], const double Ut[3], const double gd[3][3], Herm39 &h) {
   const double T0 = kT0_39;
-  double B[3][3], C[3][3][3], V[3];
-  double trB = 0.0;
+  h.trB = 0.0;
   for (int i = 0; i < 3; i++)
-    for (int j = 0; j < 3; j++) B[i][j] = gd[i][j] * T0 + Ut[i] * Ut[j];
-  for (int i = 0; i < 3; i++) trB += B[i][i];
+    for (int j = 0; j < 3; j++) h.B[i][j] = gd[i][j] * T0 + Ut[i] * Ut[j];
+  for (int i = 0; i < 3; i++) h.trB += h.B[i][i];
   // g^ij U~^k - delta^ij U^k = gd^ij U~^k + delta^ij (U~^k - U^k)
   auto term = [&](int i, int j, int k) { return gd[i][j] * Ut[k] + (i == j ? Ut[k] - U[k] : 0.0); };
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++)
       for (int k = 0; k < 3; k++)
-        C[i][j][k] = T0 * (term(i, j, k) + term(j, k, i) + term(k, i, j)) + Ut[i] * Ut[j] * Ut[k];
-  for (int i = 0; i < 3; i++) V[i] = C[i][0][0] + C[i][1][1] + C[i][2][2];
-  // the symmetric contractions over their distinct components (B and C are
-  // symmetric): c.B.c from 6 terms, C:ccc from 10
+        h.C[i][j][k] = T0 * (term(i, j, k) + term(j, k, i) + term(k, i, j)) + Ut[i] * Ut[j] * Ut[k];
+  for (int i = 0; i < 3; i++) h.V[i] = h.C[i][0][0] + h.C[i][1][1] + h.C[i][2][2];
+}
+
+// The bracket of Eq. 33 for direction c split into its even part (the same
+// for c and -c) and its odd part (opposite signs):
+//   f^eq_{+-c} = rho w {ev +- od},  ev = 1 + (c.B.c / T0 - tr B) / (2 T0),
+//   od = c.U / T0 + (C:ccc - 3 T0 c.V) / (6 T0^3),
+// with the symmetric contractions over their distinct components (c.B.c from
+// 6 terms, C:ccc from 10)
+__device__ __forceinline__ void feq39_pair(const Herm39 &h, const double U[3], double x, double y, double z,
+                                           double &ev, double &od) {
+  const double T0 = kT0_39;
+  const double cu = x * U[0] + y * U[1] + z * U[2];
+  const double cV = x * h.V[0] + y * h.V[1] + z * h.V[2];
+  const double cBc = x * x * h.B[0][0] + y * y * h.B[1][1] + z * z * h.B[2][2] +
+                     2.0 * (x * y * h.B[0][1] + x * z * h.B[0][2] + y * z * h.B[1][2]);
+  const double cCc = x * x * x * h.C[0][0][0] + y * y * y * h.C[1][1][1] + z * z * z * h.C[2][2][2] +
+                     3.0 * (x * x * y * h.C[0][0][1] + x * x * z * h.C[0][0][2] + y * y * x * h.C[1][1][0] +
+                            y * y * z * h.C[1][1][2] + z * z * x * h.C[2][2][0] + z * z * y * h.C[2][2][1]) +
+                     6.0 * x * y * z * h.C[0][1][2];
+  ev = 1.0 + (cBc / T0 - h.trB) / (2.0 * T0);
+  od = cu / T0 + (cCc - 3.0 * T0 * cV) / (6.0 * T0 * T0 * T0);
+}
+
+// Eq. 33 for every direction (used at set-up and for initialisation)
+__device__ void feq39(double rho, const double U[3], const double Ut[3], const double gd[3][3],
+                      double f[kQ39]) {
+  Herm39 h;
+  herm39(U, Ut, gd, h);
+  f[0] = rho * kT39.w[0] * (1.0 - h.trB / (2.0 * kT0_39));
 #pragma unroll 1
-  for (int a = 0; a < kQ39; a++) {
-    const double x = kT39.c[a][0], y = kT39.c[a][1], z = kT39.c[a][2];
-    const double cu = x * U[0] + y * U[1] + z * U[2];
-    const double cV = x * V[0] + y * V[1] + z * V[2];
-    const double cBc = x * x * B[0][0] + y * y * B[1][1] + z * z * B[2][2] +
-                       2.0 * (x * y * B[0][1] + x * z * B[0][2] + y * z * B[1][2]);
-    const double cCc = x * x * x * C[0][0][0] + y * y * y * C[1][1][1] + z * z * z * C[2][2][2] +
-                       3.0 * (x * x * y * C[0][0][1] + x * x * z * C[0][0][2] + y * y * x * C[1][1][0] +
-                              y * y * z * C[1][1][2] + z * z * x * C[2][2][0] + z * z * y * C[2][2][1]) +
-                       6.0 * x * y * z * C[0][1][2];
-    const double s = 1.0 + cu / T0 + (cBc / T0 - trB) / (2.0 * T0) + (cCc - 3.0 * T0 * cV) / (6.0 * T0 * T0 * T0);
-    f[a] = rho * kT39.w[a] * s;
+  for (int p = 1; p <= kH39; p++) {
+    double ev, od;
+    feq39_pair(h, U, kT39.c[p][0], kT39.c[p][1], kT39.c[p][2], ev, od);
+    f[p] = rho * kT39.w[p] * (ev + od);
+    f[p + kH39] = rho * kT39.w[p] * (ev - od);
   }
 }
 
 // One evaluation of the collision at force F (Eqs. 20, 27, 30, 31, 33):
-// post-collision N' and the updated F.
+// post-collision N' and the updated F. Directions are taken in pairs
+// (p, pbar = p + 19) with c_pbar = -c_p, so each pair's contractions are
+// formed once and split into even and odd parts.
 __device__ void eval39(const double N[kQ39], double J, double rho, const double U[3], const double F[3],
                        const double gd[3][3], const double G[3], const double *K, double tau,
                        double Np[kQ39], double Fn[3]) {
   const double T0 = kT0_39;
-  double Ut[3], feq[kQ39];
+  double Ut[3];
   for (int i = 0; i < 3; i++) Ut[i] = U[i] + 0.5 * (F[i] / rho);
-  feq39(rho, U, Ut, gd, feq);
-  // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a + K^j_abar) f^eq_a   (Eq. 30)
+  Herm39 h;
+  herm39(U, Ut, gd, h);
+  // rho w_p times the even and odd parts of each pair's bracket
+  double fe[kH39 + 1], fo[kH39 + 1];
+  fe[0] = rho * kT39.w[0] * (1.0 - h.trB / (2.0 * T0));
+  fo[0] = 0.0;
+  // deltaPi^ij = -1/2 (1 - 1/(2 tau)) sum_a c^i_a (K^j_a + K^j_abar) f^eq_a   (Eq. 30);
+  // over a pair, c_p (K_p + K_pbar) (f^eq_p - f^eq_pbar) = c_p (K_p + K_pbar) 2 rho w_p od_p
   double dP[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll 1
-  for (int a = 1; a < kQ39; a++) {
-    const int ab = opp39(a);
-    for (int i = 0; i < 3; i++) {
-      const double ci = kT39.c[a][i];
-      for (int j = 0; j < 3; j++) dP[i][j] += ci * (K[a * 3 + j] + K[ab * 3 + j]) * feq[a];
+  for (int p = 1; p <= kH39; p++) {
+    const double x = kT39.c[p][0], y = kT39.c[p][1], z = kT39.c[p][2];
+    double ev, od;
+    feq39_pair(h, U, x, y, z, ev, od);
+    const double rw = rho * kT39.w[p];
+    fe[p] = rw * ev;
+    fo[p] = rw * od;
+    const double cv[3] = {x, y, z};
+    const double d2 = 2.0 * fo[p];
+    for (int j = 0; j < 3; j++) {
+      const double m = (K[p * 3 + j] + K[(p + kH39) * 3 + j]) * d2;
+      for (int i = 0; i < 3; i++) dP[i][j] += cv[i] * m;
     }
   }
   const double cp = -0.5 * (1.0 - 1.0 / (2.0 * tau));
@@ -159,18 +194,21 @@ __device__ void eval39(const double N[kQ39], double J, double rho, const double 
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++) dP[i][j] *= cp;
   for (int i = 0; i < 3; i++) tr += dP[i][i];
+  // c.dP.c over the diagonal and the symmetrised off-diagonal components
+  const double s01 = dP[0][1] + dP[1][0], s02 = dP[0][2] + dP[2][0], s12 = dP[1][2] + dP[2][1];
   // deltaN_a = w_a J [c.F / T0 + (c.deltaPi.c / T0 - tr deltaPi) / T0]   (Eq. 31)
   // N'_a = N_a - (N_a - J f^eq_a) / tau + deltaN_a   (Eqs. 12, 20)
+  Np[0] = N[0] - (N[0] - J * fe[0]) / tau + kT39.w[0] * J * (-tr / T0);
 #pragma unroll 1
-  for (int a = 0; a < kQ39; a++) {
-    const double cv[3] = {kT39.c[a][0], kT39.c[a][1], kT39.c[a][2]};
-    double cF = 0.0, cPc = 0.0;
-    for (int i = 0; i < 3; i++) {
-      cF += cv[i] * F[i];
-      for (int j = 0; j < 3; j++) cPc += cv[i] * cv[j] * dP[i][j];
-    }
-    const double dN = kT39.w[a] * J * (cF / T0 + (cPc / T0 - tr) / T0);
-    Np[a] = N[a] - (N[a] - J * feq[a]) / tau + dN;
+  for (int p = 1; p <= kH39; p++) {
+    const double x = kT39.c[p][0], y = kT39.c[p][1], z = kT39.c[p][2];
+    const double cF = x * F[0] + y * F[1] + z * F[2];
+    const double cPc = x * x * dP[0][0] + y * y * dP[1][1] + z * z * dP[2][2] + x * y * s01 + x * z * s02 + y * z * s12;
+    const double wJ = kT39.w[p] * J;
+    const double dNe = wJ * ((cPc / T0 - tr) / T0), dNo = wJ * (cF / T0);
+    const int pb = p + kH39;
+    Np[p] = N[p] - (N[p] - J * (fe[p] + fo[p])) / tau + (dNe + dNo);
+    Np[pb] = N[pb] - (N[pb] - J * (fe[p] - fo[p])) / tau + (dNe - dNo);
   }
   // J F^i = -1/2 sum_a (K^i_a N'_a + K^i_abar N_a) + J rho G^i   (Eq. 27 and the body force)
   for (int i = 0; i < 3; i++) {
