@@ -415,9 +415,18 @@ int vlb_moments(vlb_sim *s, double *rho, double *u, double *u_tilde, double *tot
   }
   int rc = check_kernel_flags(s->d_err, s->stream);
   if (rc) return rc;
+  // the kernel writes rho [nc], u [nc][dim] and u~ [nc][dim] one after the
+  // other: one contiguous copy each, straight into the caller's arrays, in
+  // the simulation's stream, then one wait for all of them
+  double t7[7];
+  if (totals) CU(cudaMemcpyAsync(t7, s->d_totals, sizeof(t7), cudaMemcpyDeviceToHost, s->stream));
+  if (rho) CU(cudaMemcpyAsync(rho, s->d_fields, sizeof(double) * nc, cudaMemcpyDeviceToHost, s->stream));
+  if (u) CU(cudaMemcpyAsync(u, s->d_fields + nc, sizeof(double) * nc * dim, cudaMemcpyDeviceToHost, s->stream));
+  if (u_tilde)
+    CU(cudaMemcpyAsync(u_tilde, s->d_fields + nc * (1 + dim), sizeof(double) * nc * dim, cudaMemcpyDeviceToHost,
+                       s->stream));
+  CU(cudaStreamSynchronize(s->stream));
   if (totals) {
-    double t7[7];
-    CU(cudaMemcpy(t7, s->d_totals, sizeof(t7), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 7; k++) totals[k] = 0.0;
     totals[0] = t7[0];
     for (int d = 0; d < dim; d++) {
@@ -425,12 +434,6 @@ int vlb_moments(vlb_sim *s, double *rho, double *u, double *u_tilde, double *tot
       totals[4 + d] = t7[4 + d];
     }
   }
-  // the kernel writes rho [nc], u [nc][dim] and u~ [nc][dim] one after the
-  // other: one contiguous copy each, straight into the caller's arrays
-  if (rho) CU(cudaMemcpy(rho, s->d_fields, sizeof(double) * nc, cudaMemcpyDeviceToHost));
-  if (u) CU(cudaMemcpy(u, s->d_fields + nc, sizeof(double) * nc * dim, cudaMemcpyDeviceToHost));
-  if (u_tilde)
-    CU(cudaMemcpy(u_tilde, s->d_fields + nc * (1 + dim), sizeof(double) * nc * dim, cudaMemcpyDeviceToHost));
   return VLB_OK;
 }
 
