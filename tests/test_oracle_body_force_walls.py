@@ -256,3 +256,41 @@ def test_polar_walls_ghost_geometry_closed_form(wall_links):
                 else:
                     ex = _polar_theta(r, dr, dth, c[a][0], c[a][1])
                     assert np.allclose(th_a, ex, atol=1e-12, rtol=1e-12), (i, j, a, th_a, ex)
+
+
+@pytest.mark.parametrize("wall_links", [0, 1])
+def test_walls_across_a_uniform_axis(wall_links):
+    """Walls across an axis of uniform spacing (the spanwise axis of the
+    bumped, stretched channel, which is the fastest axis): the extrapolated
+    ghost nodes continue the uniform spacing, so J and g^ij are the same in
+    every cell of a row, and so is every Theta when wall-crossing links take
+    their Theta from the ghosts (wall_links = 1); with wall_links = 0 those
+    links carry Theta = 0 instead, while the interior cells of the row keep
+    the (non-zero) value that the ghosts would give."""
+    n = (8, 6, 5)
+    mesh = dict(W.channel_mesh(*n, stretch=0.7, bump=0.05, wall_links=wall_links))
+    mesh["bc"] = (W.PERIODIC, W.WALL, W.WALL)
+    shift = mesh["shift"].copy()
+    shift[2] = 0.0
+    mesh["shift"] = shift
+    g = OracleSim(mesh, W.params(0.8)).geometry()
+    J = g["J"].reshape(n)
+    ginv = g["ginv"].reshape(n + (-1,))
+    th = g["theta"].reshape(n + (19, 3, 3))
+    wl = g["wall_link"].reshape(n + (19,))
+    c, _, _ = lattice(19)
+    cz = np.array([c[a][2] for a in range(19)])
+    mid = n[2] // 2
+    assert np.abs(J - J[:, :, mid:mid + 1]).max() < 1e-14
+    assert np.abs(ginv - ginv[:, :, mid:mid + 1]).max() < 1e-14
+    for z, crossing in ((0, cz < 0), (n[2] - 1, cz > 0)):
+        assert (wl[:, :, z][:, :, crossing] == 1).all()
+        inner = th[:, :, mid][:, :, crossing]
+        assert np.abs(inner).max() > 0.05   # the readings differ on this mesh
+        got = th[:, :, z][:, :, crossing]
+        if wall_links:
+            assert np.abs(got - inner).max() < 1e-14
+        else:
+            assert np.abs(got).max() == 0.0
+        # links that stay inside the row agree in both readings
+        assert np.abs(th[:, :, z][:, :, ~crossing] - th[:, :, mid][:, :, ~crossing]).max() < 1e-14
