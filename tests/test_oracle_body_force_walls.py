@@ -35,7 +35,7 @@ import pytest
 
 from oracle import OracleSim, cell_geometry, lattice
 from oracle.build import SRC, build_oracle_copy
-from oracle.vlbo import load_library
+from oracle.vlbo import OracleError, load_library
 from paper_2401_17183_gb300 import workloads as W
 
 T0 = 1.0 / 3.0
@@ -294,3 +294,42 @@ def test_walls_across_a_uniform_axis(wall_links):
             assert np.abs(got).max() == 0.0
         # links that stay inside the row agree in both readings
         assert np.abs(th[:, :, z][:, :, ~crossing] - th[:, :, mid][:, :, ~crossing]).max() < 1e-14
+
+
+WALL_MUTATIONS = {
+    # the ghost node behind a wall copies the wall-row node instead of
+    # extrapolating linearly from the two rows inside
+    "ghost_copies_the_wall_row": ("for (int d = 0; d < 3; d++) out[d] = 2.0 * y[d] - z[d];",
+                                  "for (int d = 0; d < 3; d++) out[d] = y[d];"),
+    # the extrapolation below the lower wall skips a row
+    "ghost_stencil_skips_a_row": ("r2[a] = p[a] + 2;", "r2[a] = p[a] + 3;"),
+}
+
+
+def _wall_geometry_error(lib, wall_links):
+    """Largest deviation of g_i, J and Theta from the affine closed form on a 3D
+    affine mesh with walls on one axis (every cell, wall rows included)."""
+    A = np.array(A3)
+    n = (3, 4, 3)
+    g = OracleSim(_affine_walls(A, n, 1, wall_links), W.params(0.8), lib=lib).geometry()
+    e_g = np.abs(g["g_low"][:, :3, :3] - A.T[None]).max()
+    e_J = np.abs(g["J"] - np.linalg.det(A)).max()
+    return max(e_g, e_J, np.abs(g["theta"]).max())
+
+
+@pytest.mark.parametrize("wall_links", [0, 1])
+@pytest.mark.parametrize("name", sorted(WALL_MUTATIONS))
+def test_planted_wall_geometry_mistakes_fail_the_pins(name, wall_links, tmp_path):
+    assert _wall_geometry_error(None, wall_links) < 1e-13
+    src = open(SRC).read()
+    good, bad = WALL_MUTATIONS[name]
+    assert src.count(good) == 1, "the oracle line this mutation targets has changed"
+    lib = load_library(build_oracle_copy(src.replace(good, bad), str(tmp_path)))
+    # caught either by the closed form or, where the mistake makes a degenerate
+    # cell (a ghost on top of a node), by the oracle refusing the mesh
+    try:
+        err = _wall_geometry_error(lib, wall_links)
+    except OracleError as e:
+        assert "EGEOM" in str(e)
+        return
+    assert err > 1e-3
