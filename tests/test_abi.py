@@ -75,3 +75,41 @@ def test_errors_without_gpu_work(lib):
     rc = lib.vlb_mesh_create(ctypes.byref(d), ctypes.byref(h))
     assert rc == vlb.VLB_EINVAL and not h.value
     assert b"lattice" in lib.vlb_last_error()
+
+
+def test_empty_and_degenerate_sizes_are_rejected_on_the_host(lib):
+    """Sizes the method has no meaning for are refused by the host-side checks,
+    before any device work: an empty axis, a wall axis of one node (it has no
+    interior row to extrapolate a ghost from), a 2D mesh with n[2] != 1, a
+    D3Q39 axis shorter than its three-cell links, and a negative step count or
+    a missing simulation."""
+    from paper_2401_17183_gb300 import vlb
+    x = np.zeros(64 * 3)
+
+    def create(dim, q, n, bc):
+        d = vlb.vlb_mesh_desc()
+        d.dim, d.lattice = dim, q
+        d.x = x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        for a in range(3):
+            d.n[a] = n[a]
+            d.bc[a] = bc[a]
+        h = ctypes.c_void_p()
+        rc = lib.vlb_mesh_create(ctypes.byref(d), ctypes.byref(h))
+        assert not h.value
+        return rc, lib.vlb_last_error()
+
+    P, Wl = vlb.VLB_PERIODIC, vlb.VLB_WALL
+    cases = [
+        ((2, 9, (0, 4, 1), (P, P, P)), b"n[0]"),
+        ((3, 19, (4, 4, 0), (P, P, P)), b"n[2]"),
+        ((3, 19, (4, -3, 4), (P, P, P)), b"n[1]"),
+        ((2, 9, (4, 1, 1), (P, Wl, P)), b"wall axis"),
+        ((2, 9, (4, 4, 2), (P, P, P)), b"n[2] must be 1"),
+        ((3, 39, (4, 2, 4), (P, P, P)), b"D3Q39"),
+        ((3, 39, (4, 4, 4), (P, Wl, P)), b"D3Q39"),
+    ]
+    for args, msg in cases:
+        rc, err = create(*args)
+        assert rc == vlb.VLB_EINVAL, args
+        assert msg in err, (args, err)
+    assert lib.vlb_step(None, 1) == vlb.VLB_EINVAL
